@@ -1,0 +1,163 @@
+/*
+ * sd.h -- C ABI of the B300 exact codon-lattice design library (libsd_b300.so).
+ *
+ * The library computes, for one protein p and weight lambda >= 0 (Sec. 3,
+ * Eq. 1 of the SparseDesign paper, arXiv 2609.32308):
+ *
+ *   F*(p, lambda) = min over synonymous mRNAs r and structures S in S_{3,30}(r)
+ *                   of  E_T04,d0(r, S) + lambda * C(r),   C(r) = -sum ln w(c),
+ *
+ * by the candidate-sparsified span wavefront of Sec. 4.1 / Sec. 5 (Eqs. branch,
+ * sparse2, partitionable with S for D, candidates; Algorithm 1) over the
+ * layered weighted codon DFA of Sec. 3, on one B300 GPU, followed by a
+ * deterministic traceback of the optimal mRNA and structure.
+ *
+ * Units (Sec. 3): lambda is given in kcal/mol and multiplied by 100 inside;
+ * energies are integers in dcal/mol (0.01 kcal/mol).  Internally every DP
+ * value is an exact int64 fixed-point number in units of 2^-32 dcal/mol:
+ * E * 2^32 + sum over codons of round_half_even(100*lambda * (-ln w) * 2^32).
+ * Because this arithmetic is exact, the sparse recurrence equals the dense
+ * one bit for bit (Thm. 1) and ties are broken by a fixed canonical order.
+ *
+ * Threading: an sd_energy is immutable after loading and may be shared by
+ * host threads.  A plan is used by one host thread at a time.  All calls are
+ * synchronous unless stated; sd_plan_run is asynchronous on the given stream.
+ * Errors are returned as negative codes (sd_strerror gives the text); no call
+ * aborts the process.
+ */
+#ifndef SD_B300_H
+#define SD_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define SD_OK 0
+#define SD_EINVAL (-1)      /* invalid argument (protein, weights, lambda, file)   */
+#define SD_ERANGE (-2)      /* objective would leave the exact int64 range         */
+#define SD_EINFEASIBLE (-3) /* empty design language (no complete path)            */
+#define SD_ENOMEM (-4)      /* host or device allocation failed                    */
+#define SD_ECUDA (-5)       /* a CUDA runtime call failed                          */
+#define SD_ETIMEOUT (-6)    /* a bounded device wait expired                       */
+#define SD_EINTERNAL (-7)   /* traceback could not reproduce the DP value          */
+
+typedef struct sd_energy sd_energy; /* opaque nearest-neighbour parameter set */
+typedef struct sd_plan sd_plan;     /* opaque batch of designs resident on the GPU */
+
+/* One design (Sec. 5: the design is checked against its DFA path and a
+ * recomputed objective).  Buffers are owned by the result: sd_result_free. */
+typedef struct {
+  char *mrna;           /* n+1 bytes, A/C/G/U, NUL-terminated                       */
+  char *structure;      /* n+1 bytes, dot-bracket, NUL-terminated                   */
+  int32_t energy;       /* dcal/mol, dangle-0 free energy of (mrna, structure)      */
+  int32_t n;            /* nucleotides = 3 * codon positions                        */
+  double codon_cost;    /* C(r) = -sum ln w(c) in FP64, summed in codon order        */
+  double objective;     /* energy + (100*lambda) * codon_cost, FP64, dcal/mol        */
+  int64_t objective_fx; /* exact DP optimum, units of 2^-32 dcal/mol                */
+  int64_t Z;            /* retained candidates, sum_b |C_b| (Eq. candidates)        */
+  int64_t finite_direct;/* direct intervals with finite B (B_finite)                 */
+  int64_t retained_cells;/* finite V_t, S1, S2 cells + candidate appends            */
+  int64_t states, edges;/* DFA size N and |E|                                       */
+  int32_t regrows;      /* candidate-buffer regrow passes (0 when presized enough)  */
+  int32_t reserved;
+} sd_result;
+
+/* Load a parameter file (plain text, "SDENERGY 1" format: named integer tables
+ * stack[6][6], mismatch_{hairpin,interior,interior_1n,interior_23}[6][4][4],
+ * int11[6][6][4][4], int21[6][6][4][4][4], int22[6][6][4][4][4][4],
+ * hairpin/bulge/interior[31], terminal_au[6], ninio, max_ninio, ml_closing,
+ * ml_intern, ml_base, then "lxc <float>" and the special triloop / tetraloop /
+ * hexaloop lists "<sequence> <total>").  Pair types are AU CG GC UA GU UG;
+ * two-loop tables are indexed [outer pair][inner pair read from the loop].
+ * The model is the Turner-2004 dangle-0 model of Sec. 3 (special hairpins,
+ * lonely pairs, minimum hairpin 3, at most 30 unpaired per two-loop).
+ * On success *out owns a host copy and a device copy on the current device.
+ * Returns SD_OK, SD_EINVAL (unreadable / malformed file), SD_ENOMEM, SD_ECUDA. */
+int sd_load_energy(const char *path, sd_energy **out);
+void sd_energy_free(sd_energy *e);
+
+/* Exact design of one protein (Sec. 3, Eq. 1).
+ *   protein       one-letter amino acids, optional '*' as the last symbol only
+ *                 (an explicit stop adds a codon position; none is implied);
+ *                 may be empty.
+ *   codon_weights 64 relative adaptiveness values w(c) in (0,1], indexed
+ *                 16*x + 4*y + z with A=0 C=1 G=2 U=3; for every amino acid of
+ *                 the protein (and '*') the maximum over its codons must be 1.
+ *   lambda        >= 0, kcal/mol.
+ * Fills *out (caller-owned struct; buffers freed by sd_result_free).
+ * Returns SD_OK or SD_EINVAL / SD_ERANGE / SD_ENOMEM / SD_ECUDA / SD_EINTERNAL. */
+int sd_design(const sd_energy *energy, const char *protein, const double *codon_weights,
+              double lambda, sd_result *out);
+
+/* Exact designs of many proteins in one batched launch sequence.
+ *   proteins[count], codon_weights (count*64 values, or 64 if weights_shared),
+ *   lambdas[count]; outs[count] and status[count] are caller-owned arrays.
+ * One failing item does not stop the others; status[k] holds its code.
+ * Returns SD_OK if the batch ran (check status[]), else an error code. */
+int sd_design_batch(const sd_energy *energy, int count, const char *const *proteins,
+                    const double *codon_weights, int weights_shared, const double *lambdas,
+                    sd_result *outs, int *status);
+
+void sd_result_free(sd_result *r);
+const char *sd_strerror(int code);
+
+/* ---- plan interface: inputs resident in HBM, asynchronous execution ---- */
+
+/* Validate inputs, build every codon DFA on the host, allocate the packed
+ * tables and candidate buffers on the current device and upload the lattices.
+ * Items that fail validation are recorded in item_status (caller array of
+ * count ints, may be NULL) and skipped by sd_plan_run.  Synchronous. */
+int sd_plan_create(const sd_energy *energy, int count, const char *const *proteins,
+                   const double *codon_weights, int weights_shared, const double *lambdas,
+                   sd_plan **out, int *item_status);
+
+/* Run the fill, the exterior pass and the traceback of every valid item on
+ * `stream` (a cudaStream_t; NULL means the legacy default stream).
+ * Asynchronous: returns after enqueueing.  Re-running recomputes everything. */
+int sd_plan_run(sd_plan *plan, void *stream);
+
+/* Record CUDA events around the phases of later sd_plan_run calls (fill,
+ * exterior pass, traceback) on the run's stream; sd_plan_phase_times waits
+ * for the last timed run and returns the three durations in milliseconds. */
+int sd_plan_set_timing(sd_plan *plan, int enable);
+int sd_plan_phase_times(const sd_plan *plan, float *ms3);
+
+/* Algorithmic integer work of the fill, per item (ops[count], caller array):
+ * runs a counting variant of the fill (synchronously, on the legacy default
+ * stream) in which every min-plus term with finite operands adds
+ * 2 * (int64 additions + 1) INT32 slots.  Leaves the tables as sd_plan_run
+ * does, but without the exterior pass and the traceback. */
+int sd_plan_count_ops(sd_plan *plan, int64_t *ops);
+
+/* Number of kernel launches one sd_plan_run enqueues. */
+int64_t sd_plan_launches(const sd_plan *plan);
+
+/* Synchronise, copy results to the host and re-evaluate the FP64 objective.
+ * outs/status: caller arrays of the plan's item count. */
+int sd_plan_results(sd_plan *plan, sd_result *outs, int *status);
+
+/* Device bytes held by the plan. */
+int64_t sd_plan_device_bytes(const sd_plan *plan);
+
+/* Copy one item's tables to host arrays in the dense square layout used by
+ * tests: state ids are numbered layer by layer, inside a layer by codon
+ * prefix in ACGU order.  Arrays (any may be NULL):
+ *   layer[N] (int32); H[N*N], S1[N*N], S2[N*N], B[N*N] (int64, 2^62 = +inf);
+ *   V[N*N*6] (int64); Ext[N] (int64); cand[N*N] (uint8, cand[c*N+b] = 1 iff
+ *   c is in C_b).  Query sizes with sd_plan_item_size. Synchronous. */
+int sd_plan_item_size(const sd_plan *plan, int item, int32_t *n, int32_t *N, int32_t *E);
+int sd_plan_dump(const sd_plan *plan, int item, int32_t *layer, int64_t *H, int64_t *V,
+                 int64_t *B, int64_t *S1, int64_t *S2, int64_t *Ext, uint8_t *cand);
+/* Lattice edges of one item in (from, label) order. */
+int sd_plan_edges(const sd_plan *plan, int item, int32_t *from, int32_t *to, int32_t *label,
+                  int64_t *cost);
+void sd_plan_free(sd_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SD_B300_H */

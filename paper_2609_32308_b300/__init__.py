@@ -1,0 +1,283 @@
+"""B300-native exact codon-lattice design (SparseDesign, arXiv 2609.32308).
+
+Thin ctypes binding of libsd_b300.so (C ABI in include/sd.h): argument
+marshalling only.  Every step of the design -- the span wavefront fill, the
+exterior pass and the traceback -- runs in the library's CUDA kernels; there
+is no CPU fallback.  If the shared library is missing or cannot be loaded the
+calls raise, they never compute anything on the host.
+
+Names follow the C ABI: sd_load_energy, sd_design, sd_design_batch,
+sd_plan_create / sd_plan_run / sd_plan_results / sd_plan_dump / sd_plan_free.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsd_b300.so")
+_lib = None
+
+SD_OK, SD_EINVAL, SD_ERANGE, SD_EINFEASIBLE = 0, -1, -2, -3
+SD_ENOMEM, SD_ECUDA, SD_ETIMEOUT, SD_EINTERNAL = -4, -5, -6, -7
+INF = 1 << 62          # +infinity in table dumps
+FX_ONE = 1 << 32       # one dcal/mol in the fixed-point unit
+
+
+class SdError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {sd_strerror(code)} ({code})" if what else sd_strerror(code))
+
+
+class sd_result(ctypes.Structure):
+    _fields_ = [
+        ("mrna", ctypes.c_void_p), ("structure", ctypes.c_void_p),
+        ("energy", ctypes.c_int32), ("n", ctypes.c_int32),
+        ("codon_cost", ctypes.c_double), ("objective", ctypes.c_double),
+        ("objective_fx", ctypes.c_int64), ("Z", ctypes.c_int64),
+        ("finite_direct", ctypes.c_int64), ("retained_cells", ctypes.c_int64),
+        ("states", ctypes.c_int64), ("edges", ctypes.c_int64),
+        ("regrows", ctypes.c_int32), ("reserved", ctypes.c_int32),
+    ]
+
+
+def lib():
+    """Load libsd_b300.so (raises if it is absent: no host fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with "
+                              "`python -m paper_2609_32308_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.sd_load_energy.argtypes = [ctypes.c_char_p, ctypes.POINTER(P)]
+        L.sd_energy_free.argtypes = [P]
+        L.sd_energy_free.restype = None
+        L.sd_design.argtypes = [P, ctypes.c_char_p, P, D, ctypes.POINTER(sd_result)]
+        L.sd_design_batch.argtypes = [P, I, P, P, I, P, P, P]
+        L.sd_result_free.argtypes = [ctypes.POINTER(sd_result)]
+        L.sd_result_free.restype = None
+        L.sd_strerror.argtypes = [I]
+        L.sd_strerror.restype = ctypes.c_char_p
+        L.sd_plan_create.argtypes = [P, I, P, P, I, P, ctypes.POINTER(P), P]
+        L.sd_plan_run.argtypes = [P, P]
+        L.sd_plan_launches.argtypes = [P]
+        L.sd_plan_launches.restype = ctypes.c_int64
+        L.sd_plan_device_bytes.argtypes = [P]
+        L.sd_plan_device_bytes.restype = ctypes.c_int64
+        L.sd_plan_results.argtypes = [P, P, P]
+        L.sd_plan_item_size.argtypes = [P, I, P, P, P]
+        L.sd_plan_dump.argtypes = [P, I] + [P] * 8
+        L.sd_plan_edges.argtypes = [P, I, P, P, P, P]
+        L.sd_plan_set_timing.argtypes = [P, I]
+        L.sd_plan_count_ops.argtypes = [P, P]
+        L.sd_plan_phase_times.argtypes = [P, P]
+        L.sd_plan_free.argtypes = [P]
+        L.sd_plan_free.restype = None
+        for f in ("sd_load_energy", "sd_design", "sd_design_batch", "sd_plan_create",
+                  "sd_plan_run", "sd_plan_results", "sd_plan_item_size", "sd_plan_dump",
+                  "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
+                  "sd_plan_count_ops"):
+            getattr(L, f).restype = I
+        _lib = L
+    return _lib
+
+
+def sd_strerror(code: int) -> str:
+    try:
+        return lib().sd_strerror(int(code)).decode()
+    except ImportError:
+        return f"error {code}"
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class Energy:
+    """Loaded parameter set (host + device copy); frees itself."""
+
+    def __init__(self, path: str):
+        h = ctypes.c_void_p()
+        rc = lib().sd_load_energy(str(path).encode(), ctypes.byref(h))
+        if rc != SD_OK:
+            raise SdError(rc, f"sd_load_energy({path})")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sd_energy_free(self.handle)
+            self.handle = None
+
+
+def sd_load_energy(path: str) -> Energy:
+    return Energy(path)
+
+
+def _result_dict(r: sd_result, status: int) -> dict:
+    out = {"status": int(status)}
+    if status == SD_OK:
+        out.update(
+            mrna=ctypes.string_at(r.mrna).decode(),
+            structure=ctypes.string_at(r.structure).decode(),
+            energy=int(r.energy), n=int(r.n), codon_cost=float(r.codon_cost),
+            objective=float(r.objective), objective_fx=int(r.objective_fx), Z=int(r.Z),
+            finite_direct=int(r.finite_direct), retained_cells=int(r.retained_cells),
+            states=int(r.states), edges=int(r.edges), regrows=int(r.regrows))
+    return out
+
+
+def _weights(weights, count):
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    if w.shape == (64,):
+        return w, 1
+    w = w.reshape(count, 64)
+    return np.ascontiguousarray(w), 0
+
+
+def sd_design(energy: Energy, protein: str, weights, lam: float) -> dict:
+    """One exact design; raises SdError on failure."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+    r = sd_result()
+    rc = lib().sd_design(energy.handle, protein.encode(), _ptr(w), float(lam), ctypes.byref(r))
+    try:
+        if rc != SD_OK:
+            raise SdError(rc, "sd_design")
+        return _result_dict(r, rc)
+    finally:
+        lib().sd_result_free(ctypes.byref(r))
+
+
+def sd_design_batch(energy: Energy, proteins, weights, lambdas) -> list:
+    """Designs of many proteins; per-item dicts carry their own status."""
+    count = len(proteins)
+    w, shared = _weights(weights, count)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64).reshape(count)
+    enc = [p.encode() for p in proteins]
+    arr = (ctypes.c_char_p * count)(*enc)
+    outs = (sd_result * count)()
+    st = np.zeros(count, dtype=np.int32)
+    rc = lib().sd_design_batch(energy.handle, count, arr, _ptr(w), shared, _ptr(lam), outs,
+                               _ptr(st))
+    try:
+        if rc != SD_OK:
+            raise SdError(rc, "sd_design_batch")
+        return [_result_dict(outs[k], int(st[k])) for k in range(count)]
+    finally:
+        for k in range(count):
+            lib().sd_result_free(ctypes.byref(outs[k]))
+
+
+class Plan:
+    """A batch of designs resident on the GPU (sd_plan_* calls)."""
+
+    def __init__(self, energy: Energy, proteins, weights, lambdas):
+        self.energy = energy
+        self.count = len(proteins)
+        w, shared = _weights(weights, self.count)
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64).reshape(self.count)
+        self._keep = [p.encode() for p in proteins]
+        arr = (ctypes.c_char_p * self.count)(*self._keep)
+        self.item_status = np.zeros(self.count, dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = lib().sd_plan_create(energy.handle, self.count, arr, _ptr(w), shared, _ptr(lam),
+                                  ctypes.byref(h), _ptr(self.item_status))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        """Enqueue the whole design on `stream` (an int cudaStream_t, a torch
+        stream, or None for the legacy default stream)."""
+        s = getattr(stream, "cuda_stream", stream)
+        rc = lib().sd_plan_run(self.handle, ctypes.c_void_p(s) if s else None)
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_run")
+
+    def set_timing(self, enable: bool = True):
+        rc = lib().sd_plan_set_timing(self.handle, int(bool(enable)))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_set_timing")
+
+    def count_ops(self):
+        """Algorithmic INT32 slots of the fill, per item (counting variant)."""
+        ops = np.zeros(self.count, dtype=np.int64)
+        rc = lib().sd_plan_count_ops(self.handle, _ptr(ops))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_count_ops")
+        return ops
+
+    def phase_times(self):
+        """(fill, exterior, traceback) milliseconds of the last timed run."""
+        ms = np.zeros(3, dtype=np.float32)
+        rc = lib().sd_plan_phase_times(self.handle, _ptr(ms))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_phase_times")
+        return tuple(float(x) for x in ms)
+
+    @property
+    def launches(self) -> int:
+        return int(lib().sd_plan_launches(self.handle))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(lib().sd_plan_device_bytes(self.handle))
+
+    def results(self) -> list:
+        outs = (sd_result * self.count)()
+        st = np.zeros(self.count, dtype=np.int32)
+        rc = lib().sd_plan_results(self.handle, outs, _ptr(st))
+        try:
+            if rc != SD_OK:
+                raise SdError(rc, "sd_plan_results")
+            return [_result_dict(outs[k], int(st[k])) for k in range(self.count)]
+        finally:
+            for k in range(self.count):
+                lib().sd_result_free(ctypes.byref(outs[k]))
+
+    def size(self, item: int):
+        n, N, E = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        rc = lib().sd_plan_item_size(self.handle, item, ctypes.byref(n), ctypes.byref(N),
+                                     ctypes.byref(E))
+        return int(n.value), int(N.value), int(E.value), rc
+
+    def edges(self, item: int) -> dict:
+        _, _, E, _ = self.size(item)
+        f, t, l = (np.zeros(E, dtype=np.int32) for _ in range(3))
+        c = np.zeros(E, dtype=np.int64)
+        rc = lib().sd_plan_edges(self.handle, item, _ptr(f), _ptr(t), _ptr(l), _ptr(c))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_edges")
+        return {"from": f, "to": t, "label": l, "cost": c}
+
+    def dump(self, item: int) -> dict:
+        """Dense square-layout copies of one item's tables (tests only)."""
+        n, N, E, st = self.size(item)
+        if st != SD_OK:
+            raise SdError(st, "sd_plan_dump")
+        out = {"layer": np.zeros(N, dtype=np.int32),
+               "H": np.zeros((N, N), dtype=np.int64), "V": np.zeros((N, N, 6), dtype=np.int64),
+               "B": np.zeros((N, N), dtype=np.int64), "S1": np.zeros((N, N), dtype=np.int64),
+               "S2": np.zeros((N, N), dtype=np.int64), "Ext": np.zeros(N, dtype=np.int64),
+               "cand": np.zeros((N, N), dtype=np.uint8)}
+        rc = lib().sd_plan_dump(self.handle, item, *[_ptr(out[k]) for k in
+                                                     ("layer", "H", "V", "B", "S1", "S2", "Ext",
+                                                      "cand")])
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_dump")
+        return out
+
+    def free(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sd_plan_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
+
+
+def sd_plan_create(energy, proteins, weights, lambdas) -> Plan:
+    return Plan(energy, proteins, weights, lambdas)

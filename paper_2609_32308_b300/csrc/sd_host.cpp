@@ -1,0 +1,761 @@
+// sd_host.cpp -- host side of libsd_b300: parameter loading, codon DFA
+// construction, input validation, the exact-range check, device arenas for
+// the packed tables, batch plans and the C ABI declared in include/sd.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/sd.h"
+#include "sd_internal.h"
+
+// ---------------------------------------------------------------------------
+// energy parameters
+// ---------------------------------------------------------------------------
+struct sd_energy {
+  SdParams h;              // host copy
+  int32_t hairpin[31];     // raw hairpin length table (lengths 3..30)
+  double lxc;              // long-hairpin extrapolation coefficient
+  int32_t max_abs;         // largest |entry| over the entries the model reads
+  SdParams *d = nullptr;   // device copy
+  int device = 0;
+};
+
+namespace {
+
+bool read_table(std::istream &in, const char *name, int32_t *dst, int count) {
+  std::string word;
+  int cnt = -1;
+  if (!(in >> word >> cnt) || word != name || cnt != count) return false;
+  for (int k = 0; k < count; k++)
+    if (!(in >> dst[k])) return false;
+  return true;
+}
+
+int nt_code(char c) {
+  switch (c) {
+    case 'A': return 0;
+    case 'C': return 1;
+    case 'G': return 2;
+    case 'U': return 3;
+    default: return -1;
+  }
+}
+
+}  // namespace
+
+extern "C" int sd_load_energy(const char *path, sd_energy **out) {
+  if (!out) return SD_EINVAL;
+  *out = nullptr;
+  if (!path) return SD_EINVAL;
+  std::ifstream in(path);
+  if (!in) return SD_EINVAL;
+  sd_energy *E = new (std::nothrow) sd_energy();
+  if (!E) return SD_ENOMEM;
+  SdParams &P = E->h;
+  std::memset(&P, 0, sizeof(P));
+  std::string word;
+  int ver = 0;
+  bool ok = (in >> word >> ver) && word == "SDENERGY" && ver == 1;
+  int32_t mm[4][96];
+  int32_t bulge[31], interior[31], one[5];
+  ok = ok && read_table(in, "stack", &P.stack[0][0], 36);
+  ok = ok && read_table(in, "mismatch_hairpin", mm[0], 96);
+  ok = ok && read_table(in, "mismatch_interior", mm[1], 96);
+  ok = ok && read_table(in, "mismatch_interior_1n", mm[2], 96);
+  ok = ok && read_table(in, "mismatch_interior_23", mm[3], 96);
+  ok = ok && read_table(in, "int11", &P.int11[0][0][0], 576);
+  ok = ok && read_table(in, "int21", &P.int21[0][0][0], 2304);
+  ok = ok && read_table(in, "int22", &P.int22[0][0][0], 9216);
+  ok = ok && read_table(in, "hairpin", E->hairpin, 31);
+  ok = ok && read_table(in, "bulge", bulge, 31);
+  ok = ok && read_table(in, "interior", interior, 31);
+  ok = ok && read_table(in, "terminal_au", P.au, 6);
+  ok = ok && read_table(in, "ninio", &one[0], 1);
+  ok = ok && read_table(in, "max_ninio", &one[1], 1);
+  ok = ok && read_table(in, "ml_closing", &one[2], 1);
+  ok = ok && read_table(in, "ml_intern", &one[3], 1);
+  ok = ok && read_table(in, "ml_base", &one[4], 1);
+  ok = ok && (in >> word >> E->lxc) && word == "lxc" && std::isfinite(E->lxc);
+  const char *names[3] = {"triloop", "tetraloop", "hexaloop"};
+  const int lens[3] = {5, 6, 8};
+  for (int s = 0; s < 3 && ok; s++) {
+    int cnt = -1;
+    ok = (in >> word >> cnt) && word == names[s] && cnt >= 0 && cnt <= 64;
+    P.nspecial[s] = ok ? cnt : 0;
+    for (int k = 0; k < P.nspecial[s] && ok; k++) {
+      std::string seq;
+      int e = 0;
+      ok = (in >> seq >> e) && (int)seq.size() == lens[s];
+      int code = 0;
+      for (int q = 0; q < lens[s] && ok; q++) {
+        int c = nt_code(seq[q]);
+        ok = c >= 0;
+        code |= (c < 0 ? 0 : c) << (2 * q);
+      }
+      P.special_code[s][k] = code;
+      P.special_e[s][k] = e;
+    }
+  }
+  if (!ok) {
+    delete E;
+    return SD_EINVAL;
+  }
+  std::memcpy(P.mmH, mm[0], sizeof(mm[0]));
+  std::memcpy(P.mmI, mm[1], sizeof(mm[1]));
+  std::memcpy(P.mm1n, mm[2], sizeof(mm[2]));
+  std::memcpy(P.mm23, mm[3], sizeof(mm[3]));
+  for (int k = 0; k < 31; k++) {
+    P.bulge[k] = bulge[k];
+    P.interior[k] = interior[k];
+  }
+  P.ninio = one[0];
+  P.maxninio = one[1];
+  P.mlclosing = one[2];
+  P.mlintern = one[3];
+  P.mlbase = one[4];
+  // magnitude of every entry the model can read (loop-size tables from
+  // their smallest admissible size), for the exact-range check
+  int32_t mx = 0;
+  auto acc = [&](const int32_t *p, int cnt) {
+    for (int k = 0; k < cnt; k++) mx = std::max(mx, std::abs(p[k]));
+  };
+  acc(&P.stack[0][0], 36);
+  acc(&P.mmH[0][0], 4 * 96);
+  acc(&P.int11[0][0][0], 576 + 2304 + 9216);
+  acc(E->hairpin + 3, 28);
+  acc(P.bulge + 1, 30);
+  acc(P.interior + 2, 29);
+  acc(P.au, 6);
+  acc(one, 5);
+  for (int s = 0; s < 3; s++) acc(P.special_e[s], P.nspecial[s]);
+  E->max_abs = mx;
+  if (mx > 100000) {
+    delete E;
+    return SD_EINVAL;
+  }
+  cudaGetDevice(&E->device);
+  if (cudaMalloc(&E->d, sizeof(SdParams)) != cudaSuccess) {
+    delete E;
+    return SD_ECUDA;
+  }
+  if (cudaMemcpy(E->d, &P, sizeof(SdParams), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(E->d);
+    delete E;
+    return SD_ECUDA;
+  }
+  *out = E;
+  return SD_OK;
+}
+
+extern "C" void sd_energy_free(sd_energy *e) {
+  if (!e) return;
+  if (e->d) cudaFree(e->d);
+  delete e;
+}
+
+// ---------------------------------------------------------------------------
+// codon DFA (Sec. 3): a trie per amino acid between single codon-boundary
+// states, the whole -ln w on the third edge
+// ---------------------------------------------------------------------------
+namespace {
+
+// standard genetic code in the textbook U C A G layout
+char translate(int x, int y, int z) {
+  static const char tbl[] =
+      "FFLLSSSSYY**CC*W"
+      "LLLLPPPPHHQQRRRR"
+      "IIIMTTTTNNKKSSRR"
+      "VVVVAAAADDEEGGGG";
+  static const int ucag[4] = {2, 1, 3, 0};  // A C G U -> position in U C A G
+  return tbl[16 * ucag[x] + 4 * ucag[y] + ucag[z]];
+}
+
+struct HostLattice {
+  int n = 0, N = 0, E = 0;
+  std::vector<int32_t> lstart, layer;
+  std::vector<SdEdge> out, in;  // N*SD_MAXOUT, N*SD_MAXIN
+  std::vector<uint8_t> out_cnt, in_cnt, in_mask, out_mask;
+  std::vector<int32_t> e_from, e_to, e_label;  // (from, label) order
+  std::vector<int64_t> e_cost;
+  double qmax_sum = 0.0;  // sum over codon positions of the largest codon cost (FP64)
+};
+
+int64_t codon_fx(double lambda, double w) {
+  const double lam100 = 100.0 * lambda;
+  const double q = -std::log(w);
+  const double x = lam100 * q;
+  return (int64_t)std::llrint(std::ldexp(x, 32));
+}
+
+int build_lattice(const char *protein, const double *w, double lambda, HostLattice &L) {
+  const int A = (int)std::strlen(protein);
+  for (int k = 0; k < A; k++)
+    if (protein[k] == '*' && k != A - 1) return SD_EINVAL;
+  L.n = 3 * A;
+  L.lstart.assign(L.n + 2, 0);
+  L.layer.clear();
+  struct E3 {
+    int from, to, label;
+    int64_t cost;
+  };
+  std::vector<E3> edges;
+  L.layer.push_back(0);
+  int boundary = 0;
+  L.qmax_sum = 0.0;
+  for (int k = 0; k < A; k++) {
+    const char aa = protein[k];
+    bool used[4][4][4] = {};
+    int cnt = 0;
+    double wmax = 0.0, qmax = 0.0;
+    for (int x = 0; x < 4; x++)
+      for (int y = 0; y < 4; y++)
+        for (int z = 0; z < 4; z++) {
+          if (translate(x, y, z) != aa) continue;
+          const double ww = w[16 * x + 4 * y + z];
+          if (!(ww > 0.0 && ww <= 1.0)) return SD_EINVAL;
+          used[x][y][z] = true;
+          cnt++;
+          wmax = std::max(wmax, ww);
+          qmax = std::max(qmax, (100.0 * lambda) * -std::log(ww));
+        }
+    if (cnt == 0 || wmax != 1.0) return SD_EINVAL;
+    L.qmax_sum += qmax;
+    int first[4], pre[4][4];
+    L.lstart[3 * k + 1] = (int)L.layer.size();
+    for (int x = 0; x < 4; x++) {
+      first[x] = -1;
+      bool any = false;
+      for (int y = 0; y < 4; y++)
+        for (int z = 0; z < 4; z++) any |= used[x][y][z];
+      if (any) {
+        first[x] = (int)L.layer.size();
+        L.layer.push_back(3 * k + 1);
+      }
+    }
+    L.lstart[3 * k + 2] = (int)L.layer.size();
+    for (int x = 0; x < 4; x++)
+      for (int y = 0; y < 4; y++) {
+        pre[x][y] = -1;
+        bool any = false;
+        for (int z = 0; z < 4; z++) any |= used[x][y][z];
+        if (any) {
+          pre[x][y] = (int)L.layer.size();
+          L.layer.push_back(3 * k + 2);
+        }
+      }
+    L.lstart[3 * k + 3] = (int)L.layer.size();
+    const int next = (int)L.layer.size();
+    L.layer.push_back(3 * k + 3);
+    for (int x = 0; x < 4; x++)
+      if (first[x] >= 0) edges.push_back({boundary, first[x], x, 0});
+    for (int x = 0; x < 4; x++)
+      for (int y = 0; y < 4; y++)
+        if (pre[x][y] >= 0) edges.push_back({first[x], pre[x][y], y, 0});
+    for (int x = 0; x < 4; x++)
+      for (int y = 0; y < 4; y++)
+        for (int z = 0; z < 4; z++)
+          if (used[x][y][z])
+            edges.push_back({pre[x][y], next, z, codon_fx(lambda, w[16 * x + 4 * y + z])});
+    boundary = next;
+  }
+  L.N = (int)L.layer.size();
+  L.lstart[L.n + 1] = L.N;
+  L.E = (int)edges.size();
+  for (int l = 0; l <= L.n; l++)
+    if (L.lstart[l + 1] - L.lstart[l] > SD_W) return SD_EINVAL;
+  L.out.assign((size_t)L.N * SD_MAXOUT, SdEdge{-1, -1, 0});
+  L.in.assign((size_t)L.N * SD_MAXIN, SdEdge{-1, -1, 0});
+  L.out_cnt.assign(L.N, 0);
+  L.in_cnt.assign(L.N, 0);
+  L.in_mask.assign(L.N, 0);
+  L.out_mask.assign(L.N, 0);
+  std::vector<int> ord(edges.size());
+  for (size_t e = 0; e < edges.size(); e++) ord[e] = (int)e;
+  std::sort(ord.begin(), ord.end(), [&](int p, int q) {
+    if (edges[p].from != edges[q].from) return edges[p].from < edges[q].from;
+    return edges[p].label < edges[q].label;
+  });
+  for (int e : ord) {
+    const E3 &x = edges[e];
+    if (L.out_cnt[x.from] >= SD_MAXOUT) return SD_EINVAL;
+    L.out[(size_t)x.from * SD_MAXOUT + L.out_cnt[x.from]++] = SdEdge{x.to, x.label, x.cost};
+    L.out_mask[x.from] |= 1 << x.label;
+    L.e_from.push_back(x.from);
+    L.e_to.push_back(x.to);
+    L.e_label.push_back(x.label);
+    L.e_cost.push_back(x.cost);
+  }
+  std::sort(ord.begin(), ord.end(), [&](int p, int q) {
+    if (edges[p].to != edges[q].to) return edges[p].to < edges[q].to;
+    if (edges[p].label != edges[q].label) return edges[p].label < edges[q].label;
+    return edges[p].from < edges[q].from;
+  });
+  for (int e : ord) {
+    const E3 &x = edges[e];
+    if (L.in_cnt[x.to] >= SD_MAXIN) return SD_EINVAL;
+    L.in[(size_t)x.to * SD_MAXIN + L.in_cnt[x.to]++] = SdEdge{x.from, x.label, x.cost};
+    L.in_mask[x.to] |= 1 << x.label;
+  }
+  return SD_OK;
+}
+
+// Exact-range check: every partial-structure value must stay below 2^57 in
+// magnitude.  A structure on n nucleotides has at most n/2 + 1 loops, each of
+// at most 5 table entries plus the long-hairpin extrapolation.
+int range_check(const sd_energy *E, const HostLattice &L) {
+  const double n = L.n;
+  double lx = n > 30 ? std::fabs(E->lxc * std::log(n / 30.0)) : 0.0;
+  double ebound = (n / 2.0 + 1.0) * (5.0 * E->max_abs + lx + 1.0);
+  double total = std::ldexp(ebound, 32) + std::ldexp(L.qmax_sum, 32) + std::ldexp(n, 32);
+  return total < std::ldexp(1.0, 57) ? SD_OK : SD_ERANGE;
+}
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// plans
+// ---------------------------------------------------------------------------
+struct PlanItem {
+  std::string protein;
+  double lambda = 0.0;
+  double w[64];
+  HostLattice L;
+  int status = SD_OK;
+  int dev_index = -1;  // position in the device design array
+  SdDesign d{};        // device pointers (host copy of the struct)
+};
+
+struct sd_plan {
+  const sd_energy *energy = nullptr;
+  std::vector<PlanItem> items;
+  std::vector<SdDesign> hdesigns;
+  SdDesign *d_designs = nullptr;
+  char *arena = nullptr;
+  size_t arena_bytes = 0;
+  int max_n = 0;
+  int64_t launches = 0;
+  cudaStream_t last_stream = nullptr;
+  bool timing = false;
+  bool timed_run = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+struct Carver {
+  char *base;
+  size_t off = 0;
+  template <class T>
+  T *take(size_t count) {
+    T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+    off = align_up(off + count * sizeof(T));
+    return p;
+  }
+};
+
+// lay out one design's buffers (base == nullptr: only measure)
+size_t carve(char *base, const HostLattice &L, SdDesign &d) {
+  Carver c{base};
+  const int64_t n = L.n, N = L.N;
+  const int64_t ncell = n * (n + 1) / 2;
+  int64_t cap = 0;
+  for (int v = 0; v < N; v++) cap += L.lstart[std::max(0, L.layer[v] - 4)];
+  d.n = (int)n;
+  d.N = (int)N;
+  d.ncell = ncell;
+  d.lstart = c.take<int32_t>(n + 2);
+  d.layer = c.take<int32_t>(N);
+  d.out = c.take<SdEdge>(N * SD_MAXOUT);
+  d.out_cnt = c.take<uint8_t>(N);
+  d.in = c.take<SdEdge>(N * SD_MAXIN);
+  d.in_cnt = c.take<uint8_t>(N);
+  d.in_mask = c.take<uint8_t>(N);
+  d.out_mask = c.take<uint8_t>(N);
+  d.hp_len = c.take<int32_t>(n + 1);
+  d.H = c.take<int64_t>(ncell * SD_SLOTS);
+  d.V = c.take<int64_t>(ncell * SD_SLOTS * 6);
+  d.S1 = c.take<int64_t>(ncell * SD_SLOTS);
+  d.S2 = c.take<int64_t>(ncell * SD_SLOTS);
+  d.Bv = c.take<int64_t>(ncell * SD_SLOTS);
+  d.Ihat = c.take<int64_t>((size_t)SD_RING * (n + 1) * SD_SLOTS);
+  d.IL = c.take<int64_t>((size_t)SD_RING * (n + 1) * SD_SLOTS);
+  d.Q = c.take<int64_t>((size_t)SD_RING * (n + 1) * SD_SLOTS * 6);
+  d.cand_cnt = c.take<int32_t>(N);
+  d.cand_off = c.take<int64_t>(N);
+  d.cand_c = c.take<int32_t>(std::max<int64_t>(cap, 1));
+  d.cand_B = c.take<int64_t>(std::max<int64_t>(cap, 1));
+  d.Ext = c.take<int64_t>(N);
+  d.mrna = c.take<char>(n + 1);
+  d.structure = c.take<char>(n + 1);
+  d.tb = c.take<int64_t>(4);
+  d.tb_cap = (int)(2 * n + 64);
+  d.tb_stack = c.take<int32_t>((size_t)4 * d.tb_cap);
+  return c.off;
+}
+
+int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
+  const int64_t n = L.n, N = L.N;
+  std::vector<int32_t> hp(n + 1, 0);
+  for (int64_t Lh = 3; Lh <= n; Lh++)
+    hp[Lh] = Lh <= 30 ? E->hairpin[Lh]
+                      : E->hairpin[30] + (int32_t)(E->lxc * std::log((double)Lh / 30.0));
+  std::vector<int64_t> off(N);
+  int64_t acc = 0;
+  for (int v = 0; v < N; v++) {
+    off[v] = acc;
+    acc += L.lstart[std::max(0, L.layer[v] - 4)];
+  }
+  auto cp = [](const void *dst, const void *src, size_t bytes) {
+    return bytes == 0 || cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice) ==
+                             cudaSuccess;
+  };
+  bool ok = cp(d.lstart, L.lstart.data(), (n + 2) * 4) && cp(d.layer, L.layer.data(), N * 4) &&
+            cp(d.out, L.out.data(), L.out.size() * sizeof(SdEdge)) &&
+            cp(d.out_cnt, L.out_cnt.data(), N) &&
+            cp(d.in, L.in.data(), L.in.size() * sizeof(SdEdge)) && cp(d.in_cnt, L.in_cnt.data(), N) &&
+            cp(d.in_mask, L.in_mask.data(), N) && cp(d.out_mask, L.out_mask.data(), N) &&
+            cp(d.hp_len, hp.data(), (n + 1) * 4) && cp(d.cand_off, off.data(), N * 8);
+  return ok ? SD_OK : SD_ECUDA;
+}
+
+}  // namespace
+
+extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *const *proteins,
+                              const double *codon_weights, int weights_shared,
+                              const double *lambdas, sd_plan **out, int *item_status) {
+  if (!out) return SD_EINVAL;
+  *out = nullptr;
+  if (!energy || count < 0 || (count > 0 && (!proteins || !codon_weights || !lambdas)))
+    return SD_EINVAL;
+  sd_plan *p = new (std::nothrow) sd_plan();
+  if (!p) return SD_ENOMEM;
+  p->energy = energy;
+  p->items.resize(count);
+  size_t total = 0;
+  for (int k = 0; k < count; k++) {
+    PlanItem &it = p->items[k];
+    const double *w = codon_weights + (weights_shared ? 0 : (size_t)64 * k);
+    std::memcpy(it.w, w, sizeof(it.w));
+    it.lambda = lambdas[k];
+    if (!proteins[k] || !(std::isfinite(it.lambda) && it.lambda >= 0.0)) {
+      it.status = SD_EINVAL;
+      continue;
+    }
+    it.protein = proteins[k];
+    it.status = build_lattice(proteins[k], w, it.lambda, it.L);
+    if (it.status == SD_OK) it.status = range_check(energy, it.L);
+    if (it.status != SD_OK) continue;
+    it.dev_index = (int)p->hdesigns.size();
+    SdDesign d{};
+    total += carve(nullptr, it.L, d);
+    p->hdesigns.push_back(d);
+    p->max_n = std::max(p->max_n, it.L.n);
+  }
+  if (item_status)
+    for (int k = 0; k < count; k++) item_status[k] = p->items[k].status;
+  if (!p->hdesigns.empty()) {
+    if (cudaMalloc(&p->arena, total) != cudaSuccess) {
+      cudaGetLastError();
+      delete p;
+      return SD_ENOMEM;
+    }
+    p->arena_bytes = total;
+    size_t off = 0;
+    for (auto &it : p->items) {
+      if (it.dev_index < 0) continue;
+      SdDesign &d = p->hdesigns[it.dev_index];
+      off += carve(p->arena + off, it.L, d);
+      d.status_slot = it.dev_index;
+      it.d = d;
+      int rc = upload(energy, it.L, d);
+      if (rc != SD_OK) {
+        sd_plan_free(p);
+        return rc;
+      }
+    }
+    if (cudaMalloc(&p->d_designs, sizeof(SdDesign) * p->hdesigns.size()) != cudaSuccess ||
+        cudaMemcpy(p->d_designs, p->hdesigns.data(), sizeof(SdDesign) * p->hdesigns.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess) {
+      sd_plan_free(p);
+      return SD_ECUDA;
+    }
+  }
+  *out = p;
+  return SD_OK;
+}
+
+extern "C" int sd_plan_run(sd_plan *p, void *stream) {
+  if (!p) return SD_EINVAL;
+  p->last_stream = (cudaStream_t)stream;
+  if (p->hdesigns.empty()) return SD_OK;
+  int64_t nl = 0;
+  void *ev[4] = {p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
+  int rc = sd_k_run(p->d_designs, (int)p->hdesigns.size(), p->max_n, p->energy->d, stream, &nl,
+                    p->timing ? ev : nullptr);
+  p->launches = nl;
+  p->timed_run = p->timing;
+  return rc == 0 ? SD_OK : SD_ECUDA;
+}
+
+extern "C" int sd_plan_count_ops(sd_plan *p, int64_t *ops) {
+  if (!p || (!ops && !p->items.empty())) return SD_EINVAL;
+  const int nd = (int)p->hdesigns.size();
+  std::vector<unsigned long long> h(nd, 0);
+  if (nd > 0) {
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long) * nd) != cudaSuccess) return SD_ENOMEM;
+    int rc = sd_k_count_ops(p->d_designs, nd, p->max_n, p->energy->d, d, nullptr);
+    bool ok = rc == 0 && cudaMemcpy(h.data(), d, sizeof(unsigned long long) * nd,
+                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(d);
+    if (!ok) return SD_ECUDA;
+  }
+  for (size_t k = 0; k < p->items.size(); k++)
+    ops[k] = p->items[k].dev_index >= 0 ? (int64_t)h[p->items[k].dev_index] : 0;
+  return SD_OK;
+}
+
+extern "C" int sd_plan_set_timing(sd_plan *p, int enable) {
+  if (!p) return SD_EINVAL;
+  if (enable && !p->ev[0])
+    for (int k = 0; k < 4; k++)
+      if (cudaEventCreate(&p->ev[k]) != cudaSuccess) return SD_ECUDA;
+  p->timing = enable != 0;
+  return SD_OK;
+}
+
+extern "C" int sd_plan_phase_times(const sd_plan *p, float *ms) {
+  if (!p || !ms) return SD_EINVAL;
+  if (!p->timed_run || p->hdesigns.empty()) return SD_EINVAL;
+  if (cudaEventSynchronize(p->ev[3]) != cudaSuccess) return SD_ECUDA;
+  for (int k = 0; k < 3; k++)
+    if (cudaEventElapsedTime(&ms[k], p->ev[k], p->ev[k + 1]) != cudaSuccess) return SD_ECUDA;
+  return SD_OK;
+}
+
+extern "C" int64_t sd_plan_launches(const sd_plan *p) { return p ? p->launches : 0; }
+extern "C" int64_t sd_plan_device_bytes(const sd_plan *p) {
+  return p ? (int64_t)p->arena_bytes : 0;
+}
+
+extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
+
+extern "C" int sd_plan_results(sd_plan *p, sd_result *outs, int *status) {
+  if (!p || (!outs && !p->items.empty())) return SD_EINVAL;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return SD_ECUDA;
+  const int nd = (int)p->hdesigns.size();
+  std::vector<int64_t> counts((size_t)nd * 4, 0);
+  if (nd > 0) {
+    int64_t *d_counts = nullptr;
+    if (cudaMalloc(&d_counts, counts.size() * 8) != cudaSuccess) return SD_ENOMEM;
+    int rc = sd_k_count(p->d_designs, nd, d_counts, nullptr);
+    bool ok = rc == 0 && cudaMemcpy(counts.data(), d_counts, counts.size() * 8,
+                                    cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(d_counts);
+    if (!ok) return SD_ECUDA;
+  }
+  for (size_t k = 0; k < p->items.size(); k++) {
+    PlanItem &it = p->items[k];
+    sd_result &r = outs[k];
+    std::memset(&r, 0, sizeof(r));
+    int st = it.status;
+    if (st == SD_OK) {
+      const SdDesign &d = it.d;
+      const int n = it.L.n;
+      r.mrna = (char *)std::malloc(n + 1);
+      r.structure = (char *)std::malloc(n + 1);
+      int64_t tb[4], ext0 = 0;
+      if (!r.mrna || !r.structure) {
+        st = SD_ENOMEM;
+      } else if (cudaMemcpy(r.mrna, d.mrna, n + 1, cudaMemcpyDeviceToHost) != cudaSuccess ||
+                 cudaMemcpy(r.structure, d.structure, n + 1, cudaMemcpyDeviceToHost) !=
+                     cudaSuccess ||
+                 cudaMemcpy(tb, d.tb, sizeof(tb), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                 cudaMemcpy(&ext0, d.Ext, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        st = SD_ECUDA;
+      } else {
+        r.mrna[n] = 0;
+        r.structure[n] = 0;
+        r.n = n;
+        r.energy = (int32_t)tb[0];
+        r.objective_fx = ext0;
+        if (ext0 >= SD_FINLIM) st = SD_EINFEASIBLE;
+        else if (tb[2] != 0 || tb[0] * 4294967296LL + tb[1] != ext0) st = SD_EINTERNAL;
+        // FP64 objective from the emitted codons, in codon order
+        double cc = 0.0;
+        for (int c = 0; st == SD_OK && c + 2 < n; c += 3) {
+          int x = nt_code(r.mrna[c]), y = nt_code(r.mrna[c + 1]), z = nt_code(r.mrna[c + 2]);
+          if (x < 0 || y < 0 || z < 0) {
+            st = SD_EINTERNAL;
+            break;
+          }
+          cc += -std::log(it.w[16 * x + 4 * y + z]);
+        }
+        r.codon_cost = cc;
+        r.objective = (double)r.energy + (100.0 * it.lambda) * cc;
+        const int64_t *c4 = &counts[(size_t)it.dev_index * 4];
+        r.Z = c4[0];
+        r.finite_direct = c4[1];
+        r.retained_cells = c4[2];
+        r.states = it.L.N;
+        r.edges = it.L.E;
+        r.regrows = 0;
+      }
+    }
+    if (status) status[k] = st;
+  }
+  return SD_OK;
+}
+
+extern "C" int sd_plan_item_size(const sd_plan *p, int item, int32_t *n, int32_t *N, int32_t *E) {
+  if (!p || item < 0 || item >= (int)p->items.size()) return SD_EINVAL;
+  const PlanItem &it = p->items[item];
+  if (n) *n = it.L.n;
+  if (N) *N = it.L.N;
+  if (E) *E = it.L.E;
+  return it.status;
+}
+
+extern "C" int sd_plan_edges(const sd_plan *p, int item, int32_t *from, int32_t *to,
+                             int32_t *label, int64_t *cost) {
+  if (!p || item < 0 || item >= (int)p->items.size()) return SD_EINVAL;
+  const HostLattice &L = p->items[item].L;
+  for (int e = 0; e < L.E; e++) {
+    if (from) from[e] = L.e_from[e];
+    if (to) to[e] = L.e_to[e];
+    if (label) label[e] = L.e_label[e];
+    if (cost) cost[e] = L.e_cost[e];
+  }
+  return SD_OK;
+}
+
+extern "C" int sd_plan_dump(const sd_plan *p, int item, int32_t *layer, int64_t *H, int64_t *V,
+                            int64_t *B, int64_t *S1, int64_t *S2, int64_t *Ext, uint8_t *cand) {
+  if (!p || item < 0 || item >= (int)p->items.size()) return SD_EINVAL;
+  const PlanItem &it = p->items[item];
+  if (it.status != SD_OK) return it.status;
+  if (cudaDeviceSynchronize() != cudaSuccess) return SD_ECUDA;
+  const HostLattice &L = it.L;
+  const SdDesign &d = it.d;
+  const int64_t n = L.n, N = L.N, NN = N * N;
+  const int64_t slots = d.ncell * SD_SLOTS;
+  auto fetch = [](std::vector<int64_t> &v, const int64_t *src, int64_t count) {
+    v.resize(count);
+    return count == 0 ||
+           cudaMemcpy(v.data(), src, count * 8, cudaMemcpyDeviceToHost) == cudaSuccess;
+  };
+  std::vector<int64_t> h, vv, b, s1, s2, ext;
+  if ((H && !fetch(h, d.H, slots)) || (V && !fetch(vv, d.V, slots * 6)) ||
+      (B && !fetch(b, d.Bv, slots)) || (S1 && !fetch(s1, d.S1, slots)) ||
+      (S2 && !fetch(s2, d.S2, slots)) || (Ext && !fetch(ext, d.Ext, N)))
+    return SD_ECUDA;
+  auto cv = [](int64_t x) { return x >= SD_FINLIM ? (int64_t)SD_EXT_INF : x; };
+  if (layer)
+    for (int v = 0; v < N; v++) layer[v] = L.layer[v];
+  for (int64_t k = 0; k < NN; k++) {
+    if (H) H[k] = SD_EXT_INF;
+    if (B) B[k] = SD_EXT_INF;
+    if (S1) S1[k] = SD_EXT_INF;
+    if (S2) S2[k] = SD_EXT_INF;
+    if (V)
+      for (int t = 0; t < 6; t++) V[k * 6 + t] = SD_EXT_INF;
+    if (cand) cand[k] = 0;
+  }
+  for (int a = 0; a < N; a++)
+    for (int bb = L.lstart[L.layer[a] + 1]; bb < N; bb++) {
+      const int la = L.layer[a], lb = L.layer[bb];
+      const int64_t g = lb - la;
+      const int64_t s = (((g - 1) * (n + 1) - (g - 1) * g / 2) + la) * SD_SLOTS +
+                        (a - L.lstart[la]) * SD_W + (bb - L.lstart[lb]);
+      const int64_t q = (int64_t)a * N + bb;
+      if (H) H[q] = cv(h[s]);
+      if (B) B[q] = cv(b[s]);
+      if (S1) S1[q] = cv(s1[s]);
+      if (S2) S2[q] = cv(s2[s]);
+      if (V)
+        for (int t = 0; t < 6; t++) V[q * 6 + t] = cv(vv[s * 6 + t]);
+    }
+  if (Ext)
+    for (int v = 0; v < N; v++) Ext[v] = cv(ext[v]);
+  if (cand) {
+    std::vector<int32_t> cnt(N), cc;
+    std::vector<int64_t> off(N);
+    if (cudaMemcpy(cnt.data(), d.cand_cnt, N * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(off.data(), d.cand_off, N * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+      return SD_ECUDA;
+    for (int bb = 0; bb < N; bb++) {
+      cc.resize(std::max(cnt[bb], 1));
+      if (cnt[bb] > 0 && cudaMemcpy(cc.data(), d.cand_c + off[bb], (size_t)cnt[bb] * 4,
+                                    cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SD_ECUDA;
+      for (int k = 0; k < cnt[bb]; k++) cand[(int64_t)cc[k] * N + bb] = 1;
+    }
+  }
+  return SD_OK;
+}
+
+extern "C" void sd_plan_free(sd_plan *p) {
+  if (!p) return;
+  if (p->arena) cudaFree(p->arena);
+  if (p->d_designs) cudaFree(p->d_designs);
+  for (int k = 0; k < 4; k++)
+    if (p->ev[k]) cudaEventDestroy(p->ev[k]);
+  delete p;
+}
+
+// ---------------------------------------------------------------------------
+// one-call conveniences
+// ---------------------------------------------------------------------------
+extern "C" int sd_design_batch(const sd_energy *energy, int count, const char *const *proteins,
+                               const double *codon_weights, int weights_shared,
+                               const double *lambdas, sd_result *outs, int *status) {
+  if (!energy || count < 0 || (count > 0 && (!outs || !status))) return SD_EINVAL;
+  sd_plan *p = nullptr;
+  int rc = sd_plan_create(energy, count, proteins, codon_weights, weights_shared, lambdas, &p,
+                          status);
+  if (rc != SD_OK) return rc;
+  rc = sd_plan_run(p, nullptr);
+  if (rc == SD_OK) rc = sd_plan_results(p, outs, status);
+  sd_plan_free(p);
+  return rc;
+}
+
+extern "C" int sd_design(const sd_energy *energy, const char *protein, const double *codon_weights,
+                         double lambda, sd_result *out) {
+  if (!energy || !protein || !codon_weights || !out) return SD_EINVAL;
+  int st = SD_OK;
+  int rc = sd_design_batch(energy, 1, &protein, codon_weights, 1, &lambda, out, &st);
+  return rc != SD_OK ? rc : st;
+}
+
+extern "C" void sd_result_free(sd_result *r) {
+  if (!r) return;
+  std::free(r->mrna);
+  std::free(r->structure);
+  r->mrna = r->structure = nullptr;
+}
+
+extern "C" const char *sd_strerror(int code) {
+  switch (code) {
+    case SD_OK: return "ok";
+    case SD_EINVAL: return "invalid argument";
+    case SD_ERANGE: return "objective outside the exact fixed-point range";
+    case SD_EINFEASIBLE: return "empty design language";
+    case SD_ENOMEM: return "out of memory";
+    case SD_ECUDA: return "CUDA runtime error";
+    case SD_ETIMEOUT: return "bounded device wait expired";
+    case SD_EINTERNAL: return "traceback did not reproduce the DP value";
+    default: return "unknown error";
+  }
+}

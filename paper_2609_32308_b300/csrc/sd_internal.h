@@ -1,0 +1,100 @@
+// sd_internal.h -- data layout shared by the host library and the kernels.
+//
+// Lattice: the layered codon DFA of Sec. 3.  States are numbered layer by
+// layer; lstart[l] is the first state of layer l (lstart[n+1] = N).  Every
+// layer holds at most SD_W states (the codon trie of the standard code has
+// width 2: Leu, Ser, Arg and the stop have two first nucleotides / prefixes).
+//
+// Tables are "forward packed" by span (the paper's packed layout omits the
+// reverse-layer slots): the cells of layer pair (i, i+g), g >= 1, form
+// diagonal g; diagonal g starts at cell D(g) = (g-1)(n+1) - (g-1)g/2 and
+// layer pair (i, i+g) is cell D(g) + i.  Each cell holds SD_W * SD_W state-pair
+// slots (slot = sa*SD_W + sb, sa/sb = state offsets inside their layers), so a
+// warp working on consecutive i of one diagonal touches consecutive memory.
+#pragma once
+#include <stdint.h>
+
+#define SD_W 2
+#define SD_SLOTS (SD_W * SD_W)
+#define SD_MAXOUT 4      // out-edges per state (one per label in a DFA)
+#define SD_MAXIN 8       // in-edges per state (codon trie: at most 6)
+#define SD_RING 32       // diagonals kept for the windowed two-loop tables
+#define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
+
+// +infinity and the finiteness threshold of the fixed-point arithmetic.
+// Stored values are either SD_INF or finite with |v| < 2^57 (checked on the
+// host before a design runs), so a sum of at most four stored operands is
+// finite iff it is < 2^59, and never overflows.
+#define SD_INF (1LL << 60)
+#define SD_FINLIM (1LL << 59)
+#define SD_EXT_INF (1LL << 62)   // +inf in the dense dump layout
+
+struct SdEdge {
+  int32_t other;   // target state (out-edges) or source state (in-edges)
+  int32_t label;   // nucleotide 0..3 = A C G U
+  int64_t cost;    // fixed-point codon cost (non-zero only on 3rd codon edges)
+};
+
+// Nearest-neighbour parameters on the device (integer dcal/mol).
+struct SdParams {
+  int32_t stack[6][6];
+  int32_t mmH[6][16], mmI[6][16], mm1n[6][16], mm23[6][16];
+  int32_t int11[6][6][16];
+  int32_t int21[6][6][64];
+  int32_t int22[6][6][256];
+  int32_t bulge[32], interior[32];
+  int32_t au[6];
+  int32_t ninio, maxninio, mlclosing, mlintern, mlbase;
+  int32_t nspecial[3];          // triloops (5 nt), tetraloops (6 nt), hexaloops (8 nt)
+  int32_t special_code[3][64];  // 2 bits per nucleotide, first nucleotide lowest
+  int32_t special_e[3][64];
+};
+
+// One design resident on the device.
+struct SdDesign {
+  int32_t n, N;           // nucleotides, states
+  int32_t status_slot;    // index into the plan's status array
+  int32_t pad;
+  const int32_t *lstart;  // n+2
+  const int32_t *layer;   // N
+  const SdEdge *out;      // N * SD_MAXOUT, by label
+  const uint8_t *out_cnt; // N
+  const SdEdge *in;       // N * SD_MAXIN, by (label, source)
+  const uint8_t *in_cnt;  // N
+  const uint8_t *in_mask; // N, bit l set iff some edge with label l enters the state
+  const uint8_t *out_mask;// N, bit l set iff the state has an out-edge with label l
+  const int32_t *hp_len;  // hairpin length energy for L = 0..n (lxc extrapolation > 30)
+  int64_t *H;             // ncell*SLOTS  min path cost between states
+  int64_t *V;             // ncell*SLOTS*6 typed closed values V_t(a,b)
+  int64_t *S1, *S2;       // ncell*SLOTS  sparse one- / two-branch multiloop values
+  int64_t *Bv;            // ncell*SLOTS  branch interface B(a,b) = min_t V_t + beta_t
+  int64_t *Ihat;          // SD_RING*(n+1)*SLOTS inner pair + its loop-side mismatch
+  int64_t *IL;            // SD_RING*(n+1)*SLOTS generic internal loops below a pair
+  int64_t *Q;             // SD_RING*(n+1)*SLOTS*6 closed-interior values per outer type
+  int32_t *cand_cnt;      // N   |C_b|
+  const int64_t *cand_off;// N   first entry of C_b
+  int32_t *cand_c;        // start states of the retained candidates
+  int64_t *cand_B;        // their scalar branch costs B(c,b)
+  int64_t *Ext;           // N   exterior suffix values (Sec. 5 final-column exterior)
+  char *mrna, *structure; // n+1 each
+  int64_t *tb;            // traceback output: [0] energy, [1] path cost, [2] status
+  int32_t *tb_stack;      // traceback work list, 4 ints per task
+  int32_t tb_cap;         // tasks
+  int32_t pad2;
+  int64_t ncell;          // n(n+1)/2
+};
+
+// Host entry points implemented in sd_kernels.cu.
+#ifdef __cplusplus
+extern "C" {
+#endif
+// events: NULL or four cudaEvent_t recorded before the fill, after the fill,
+// after the exterior pass and after the traceback, on `stream`
+int sd_k_run(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
+             void *stream, int64_t *launches, void *const *events);
+int sd_k_count_ops(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
+                   unsigned long long *d_ops, void *stream);
+int sd_k_clear(const SdDesign *h_designs, const SdDesign *d_designs, int count, void *stream);
+#ifdef __cplusplus
+}
+#endif

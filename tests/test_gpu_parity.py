@@ -1,0 +1,191 @@
+"""CUDA path vs the CPU oracle, element by element (marked gpu).
+
+Sparse GPU tables (S1, S2, candidate sets) must equal the dense oracle's
+(D1, D2, C_b by definition) bit for bit at every cell (Thm. 1 in exact
+integer arithmetic), as must the typed closed values, the branch interface,
+the exterior values, the lattice and the canonical design.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import evaluate
+from oracle.params import read_params
+from paper_2609_32308_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sd():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2609_32308_b300 as sd
+    sd.lib()
+    return sd
+
+
+@pytest.fixture(scope="module")
+def E1(sd, par1):
+    return sd.sd_load_energy(par1)
+
+
+@pytest.fixture(scope="module")
+def Emlb(sd, par_mlbase):
+    return sd.sd_load_energy(par_mlbase)
+
+
+def compare_tables(plan, item, o):
+    d = plan.dump(item)
+    N = o.N
+    assert d["layer"].tolist() == o.layer.tolist()
+    # gap cells: only pairs with a later layer are defined
+    later = o.layer[None, :] > o.layer[:, None]
+    assert np.array_equal(np.where(later, d["H"], 0), np.where(later, o.H, 0))
+    assert np.array_equal(d["V"], o.V)
+    assert np.array_equal(d["B"], o.B)
+    assert np.array_equal(d["S1"], o.D1)
+    assert np.array_equal(d["S2"], o.D2)
+    assert np.array_equal(d["Ext"], o.Ext)
+    assert np.array_equal(d["cand"], o.cand)
+    assert N == d["layer"].size
+
+
+def compare_design(r, o, lam):
+    assert r["status"] == 0
+    assert r["mrna"] == o.mrna
+    assert r["structure"] == o.structure
+    assert r["energy"] == o.energy
+    assert r["objective_fx"] == o.obj_fx
+    assert r["codon_cost"] == o.codon_cost
+    assert abs(r["objective"] - o.objective) <= 1e-9
+    assert r["objective"] == o.objective
+    assert r["Z"] == o.Z
+    assert r["finite_direct"] == o.finite_direct
+    assert r["retained_cells"] == o.retained_cells
+    assert r["states"] == o.N
+
+
+CASES = [(40, 1, 0.0), (40, 2, 4.0), (25, 3, 1.5), (60, 4, 4.0), (12, 5, 0.0), (90, 6, 4.0)]
+
+
+@pytest.mark.parametrize("A,seed,lam", CASES)
+def test_tables_and_design_match_oracle(sd, E1, par1, A, seed, lam):
+    prot = inputs.random_protein(A, seed)
+    w = inputs.random_codon_weights(seed)
+    o = oracle.run(par1, prot, w, lam)
+    assert o.status == 0
+    plan = sd.Plan(E1, [prot], w, [lam])
+    plan.run()
+    res = plan.results()
+    compare_tables(plan, 0, o)
+    compare_design(res[0], o, lam)
+    plan.free()
+
+
+def test_nonzero_ml_base(sd, Emlb, par_mlbase):
+    prot = inputs.random_protein(45, 21)
+    w = inputs.random_codon_weights(21)
+    for lam in (0.0, 2.0):
+        o = oracle.run(par_mlbase, prot, w, lam)
+        plan = sd.Plan(Emlb, [prot], w, [lam])
+        plan.run()
+        res = plan.results()
+        compare_tables(plan, 0, o)
+        compare_design(res[0], o, lam)
+
+
+def test_lattice_matches_oracle(sd, E1, par1):
+    prot = "MLSRW*"
+    w = inputs.random_codon_weights(8)
+    o = oracle.run(par1, prot, w, 4.0)
+    plan = sd.Plan(E1, [prot], w, [4.0])
+    e = plan.edges(0)
+    assert e["from"].tolist() == o.edge_from.tolist()
+    assert e["to"].tolist() == o.edge_to.tolist()
+    assert e["label"].tolist() == o.edge_label.tolist()
+    assert e["cost"].tolist() == o.edge_cost.tolist()
+
+
+def test_batch_of_mixed_lengths_and_lambdas(sd, E1, par1):
+    lengths = [5, 33, 18, 41, 1, 27]
+    batch = inputs.protein_batch(lengths, seed=77)
+    prots = [b[0] for b in batch]
+    ws = np.stack([b[1] for b in batch])
+    lams = [b[2] for b in batch]
+    res = sd.sd_design_batch(E1, prots, ws, lams)
+    for (p, w, lam), r in zip(batch, res):
+        o = oracle.run(par1, p, w, lam)
+        compare_design(r, o, lam)
+
+
+def test_edge_cases(sd, E1, par1):
+    w = inputs.random_codon_weights(1)
+    r = sd.sd_design(E1, "", w, 4.0)
+    assert r["mrna"] == "" and r["structure"] == "" and r["energy"] == 0
+    r = sd.sd_design(E1, "M", w, 4.0)
+    assert r["mrna"] == "AUG" and r["structure"] == "..."
+    bad_w = w.copy()
+    bad_w[inputs.codon_index("AUG")] = 0.5
+    res = sd.sd_design_batch(E1, ["MK", "M*K", "MBK", "MKL", "M"], np.stack([w, w, w, w, bad_w]),
+                             [1.0, 1.0, 1.0, -1.0, 1.0])
+    assert [r["status"] for r in res] == [0, sd.SD_EINVAL, sd.SD_EINVAL, sd.SD_EINVAL,
+                                          sd.SD_EINVAL]
+    o = oracle.run(par1, "MK", w, 1.0)
+    compare_design(res[0], o, 1.0)
+    # an objective outside the exact int64 range is refused, not wrapped
+    tiny = np.full(64, 1e-300)
+    for aa in "ACDEFGHIKLMNPQRSTVWY*":
+        tiny[inputs.codon_index(inputs.synonymous_codons(aa)[0])] = 1.0
+    with pytest.raises(sd.SdError) as ei:
+        sd.sd_design(E1, "LLLLLLLLLLLL", tiny, 1e6)
+    assert ei.value.code == sd.SD_ERANGE
+
+
+def test_rerun_is_deterministic(sd, E1):
+    prot = inputs.random_protein(50, 9)
+    w = inputs.random_codon_weights(9)
+    plan = sd.Plan(E1, [prot], w, [4.0])
+    plan.run()
+    a = plan.results()[0]
+    da = plan.dump(0)
+    plan.run()
+    b = plan.results()[0]
+    db = plan.dump(0)
+    assert a == b
+    for k in da:
+        assert np.array_equal(da[k], db[k])
+
+
+def _design_properties(P, prot, w, lam, r):
+    mrna = r["mrna"]
+    assert "".join(inputs.GENETIC_CODE[mrna[k:k + 3]] for k in range(0, len(mrna), 3)) == prot
+    assert evaluate.energy(P, mrna, r["structure"]) == r["energy"]
+    assert evaluate.max_two_loop_unpaired(r["structure"]) <= 30
+    codons = [mrna[k:k + 3] for k in range(0, len(mrna), 3)]
+    qsum = sum(round(math.ldexp((100.0 * lam) * (-math.log(w[inputs.codon_index(c)])), 32))
+               for c in codons)
+    assert r["objective_fx"] == (r["energy"] << 32) + qsum
+    cc = 0.0
+    for c in codons:
+        cc += -math.log(w[inputs.codon_index(c)])
+    assert r["codon_cost"] == cc
+    assert r["objective"] == float(r["energy"]) + (100.0 * lam) * cc
+    # the DP residual is within the fixed-point quantisation bound
+    assert abs(r["objective_fx"] / 2**32 - r["objective"]) <= len(codons) * 2.0**-32 + 1e-6
+
+
+@pytest.mark.parametrize("A,lam", [(925, 4.0), (925, 0.0)])
+def test_full_size_design_properties(sd, E1, par1, A, lam):
+    """925 aa (2,775 nt) at the launch configuration bench.py times: the
+    design translates back, its re-evaluated energy and objective equal the
+    DP value exactly, and every two-loop respects the 30-nt cap."""
+    P = read_params(par1)
+    prot = inputs.random_protein(A, 925)
+    w = inputs.random_codon_weights(925)
+    r = sd.sd_design(E1, prot, w, lam)
+    _design_properties(P, prot, w, lam, r)
+    assert 0 < r["Z"] <= r["finite_direct"]
