@@ -383,19 +383,29 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.in_mask = c.take<uint8_t>(N);
   d.out_mask = c.take<uint8_t>(N);
   d.hp_len = c.take<int32_t>(n + 1);
+  const size_t ring = (size_t)SD_RING * (n + 1) * SD_SLOTS;
   d.H = c.take<int64_t>(ncell * SD_SLOTS);
+  d.Hk = c.take<uint8_t>(ncell * SD_SLOTS);
   d.V = c.take<int64_t>(ncell * SD_SLOTS * 6);
+  d.Vk = c.take<uint32_t>(ncell * SD_SLOTS * 6);
   d.S1 = c.take<int64_t>(ncell * SD_SLOTS);
+  d.S1k = c.take<uint32_t>(ncell * SD_SLOTS);
   d.S2 = c.take<int64_t>(ncell * SD_SLOTS);
+  d.S2k = c.take<uint32_t>(ncell * SD_SLOTS);
   d.Bv = c.take<int64_t>(ncell * SD_SLOTS);
-  d.Ihat = c.take<int64_t>((size_t)SD_RING * (n + 1) * SD_SLOTS);
-  d.IL = c.take<int64_t>((size_t)SD_RING * (n + 1) * SD_SLOTS);
-  d.Q = c.take<int64_t>((size_t)SD_RING * (n + 1) * SD_SLOTS * 6);
+  d.Bk = c.take<uint8_t>(ncell * SD_SLOTS);
+  d.Ihat = c.take<int64_t>(ring);
+  d.Ihk = c.take<uint32_t>(ring);
+  d.IL = c.take<int64_t>(ring);
+  d.ILk = c.take<uint32_t>(ring);
+  d.Q = c.take<int64_t>(ring * 6);
+  d.Qk = c.take<uint32_t>(ring * 6);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
   d.cand_c = c.take<int32_t>(std::max<int64_t>(cap, 1));
   d.cand_B = c.take<int64_t>(std::max<int64_t>(cap, 1));
   d.Ext = c.take<int64_t>(N);
+  d.Extk = c.take<uint32_t>(N);
   d.mrna = c.take<char>(n + 1);
   d.structure = c.take<char>(n + 1);
   d.tb = c.take<int64_t>(4);

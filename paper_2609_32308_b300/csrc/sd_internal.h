@@ -64,18 +64,28 @@ struct SdDesign {
   const uint8_t *in_mask; // N, bit l set iff some edge with label l enters the state
   const uint8_t *out_mask;// N, bit l set iff the state has an out-edge with label l
   const int32_t *hp_len;  // hairpin length energy for L = 0..n (lxc extrapolation > 30)
+  // Every value comes with the canonical key of the option attaining it (the
+  // lexicographically smallest (value, key)); the traceback follows keys.
   int64_t *H;             // ncell*SLOTS  min path cost between states
+  uint8_t *Hk;            // ncell*SLOTS  (first, last) label of the first min-cost path
   int64_t *V;             // ncell*SLOTS*6 typed closed values V_t(a,b)
+  uint32_t *Vk;           // ncell*SLOTS*6
   int64_t *S1, *S2;       // ncell*SLOTS  sparse one- / two-branch multiloop values
+  uint32_t *S1k, *S2k;    // ncell*SLOTS
   int64_t *Bv;            // ncell*SLOTS  branch interface B(a,b) = min_t V_t + beta_t
+  uint8_t *Bk;            // ncell*SLOTS  attaining pair type
   int64_t *Ihat;          // SD_RING*(n+1)*SLOTS inner pair + its loop-side mismatch
+  uint32_t *Ihk;
   int64_t *IL;            // SD_RING*(n+1)*SLOTS generic internal loops below a pair
+  uint32_t *ILk;
   int64_t *Q;             // SD_RING*(n+1)*SLOTS*6 closed-interior values per outer type
+  uint32_t *Qk;
   int32_t *cand_cnt;      // N   |C_b|
   const int64_t *cand_off;// N   first entry of C_b
   int32_t *cand_c;        // start states of the retained candidates
   int64_t *cand_B;        // their scalar branch costs B(c,b)
   int64_t *Ext;           // N   exterior suffix values (Sec. 5 final-column exterior)
+  uint32_t *Extk;         // N
   char *mrna, *structure; // n+1 each
   int64_t *tb;            // traceback output: [0] energy, [1] path cost, [2] status
   int32_t *tb_stack;      // traceback work list, 4 ints per task
