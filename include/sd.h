@@ -83,7 +83,7 @@ void sd_energy_free(sd_energy *e);
 /* Exact design of one protein (Sec. 3, Eq. 1).
  *   protein       one-letter amino acids, optional '*' as the last symbol only
  *                 (an explicit stop adds a codon position; none is implied);
- *                 may be empty.
+ *                 may be empty; at most 4000 codon positions (12,000 nt).
  *   codon_weights 64 relative adaptiveness values w(c) in (0,1], indexed
  *                 16*x + 4*y + z with A=0 C=1 G=2 U=3; for every amino acid of
  *                 the protein (and '*') the maximum over its codons must be 1.
@@ -132,6 +132,15 @@ int sd_plan_phase_times(const sd_plan *plan, float *ms3);
  * 2 * (int64 additions + 1) INT32 slots.  Leaves the tables as sd_plan_run
  * does, but without the exterior pass and the traceback. */
 int sd_plan_count_ops(sd_plan *plan, int64_t *ops);
+
+/* Threads cooperating on one layer pair in the fill: 1, 8 or 32 (default 8).
+ * Results do not depend on it; speed does (1 suits large batches, 32 a single
+ * design).  sd_plan_autotune runs the plan once per candidate (synchronously,
+ * legacy default stream), keeps the fastest and writes the three fill times
+ * (ms, in the order 1, 8, 32) to ms3 (may be NULL). */
+int sd_plan_set_group(sd_plan *plan, int group);
+int sd_plan_get_group(const sd_plan *plan);
+int sd_plan_autotune(sd_plan *plan, float *ms3);
 
 /* Number of kernel launches one sd_plan_run enqueues. */
 int64_t sd_plan_launches(const sd_plan *plan);

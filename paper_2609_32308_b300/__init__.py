@@ -74,13 +74,17 @@ def lib():
         L.sd_plan_edges.argtypes = [P, I, P, P, P, P]
         L.sd_plan_set_timing.argtypes = [P, I]
         L.sd_plan_count_ops.argtypes = [P, P]
+        L.sd_plan_set_group.argtypes = [P, I]
+        L.sd_plan_get_group.argtypes = [P]
+        L.sd_plan_autotune.argtypes = [P, P]
         L.sd_plan_phase_times.argtypes = [P, P]
         L.sd_plan_free.argtypes = [P]
         L.sd_plan_free.restype = None
         for f in ("sd_load_energy", "sd_design", "sd_design_batch", "sd_plan_create",
                   "sd_plan_run", "sd_plan_results", "sd_plan_item_size", "sd_plan_dump",
                   "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
-                  "sd_plan_count_ops"):
+                  "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
+                  "sd_plan_autotune"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -201,6 +205,24 @@ class Plan:
         rc = lib().sd_plan_set_timing(self.handle, int(bool(enable)))
         if rc != SD_OK:
             raise SdError(rc, "sd_plan_set_timing")
+
+    @property
+    def group(self) -> int:
+        return int(lib().sd_plan_get_group(self.handle))
+
+    @group.setter
+    def group(self, g: int):
+        rc = lib().sd_plan_set_group(self.handle, int(g))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_set_group")
+
+    def autotune(self):
+        """Pick the fastest group size; returns {group: fill ms}."""
+        ms = np.zeros(3, dtype=np.float32)
+        rc = lib().sd_plan_autotune(self.handle, _ptr(ms))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_autotune")
+        return dict(zip((1, 8, 32), (float(x) for x in ms)))
 
     def count_ops(self):
         """Algorithmic INT32 slots of the fill, per item (counting variant)."""

@@ -346,6 +346,7 @@ struct sd_plan {
   int max_n = 0;
   int64_t launches = 0;
   cudaStream_t last_stream = nullptr;
+  int group = 8;  // threads per layer pair in the fill
   bool timing = false;
   bool timed_run = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -400,6 +401,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.ILk = c.take<uint32_t>(ring);
   d.Q = c.take<int64_t>(ring * 6);
   d.Qk = c.take<uint32_t>(ring * 6);
+  d.W = c.take<int64_t>(ring * SD_WN);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
   d.cand_c = c.take<int32_t>(std::max<int64_t>(cap, 1));
@@ -464,6 +466,7 @@ extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *co
     }
     it.protein = proteins[k];
     it.status = build_lattice(proteins[k], w, it.lambda, it.L);
+    if (it.status == SD_OK && it.L.n > SD_MAX_NT) it.status = SD_EINVAL;
     if (it.status == SD_OK) it.status = range_check(energy, it.L);
     if (it.status != SD_OK) continue;
     it.dev_index = (int)p->hdesigns.size();
@@ -512,7 +515,7 @@ extern "C" int sd_plan_run(sd_plan *p, void *stream) {
   int64_t nl = 0;
   void *ev[4] = {p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
   int rc = sd_k_run(p->d_designs, (int)p->hdesigns.size(), p->max_n, p->energy->d, stream, &nl,
-                    p->timing ? ev : nullptr);
+                    p->timing ? ev : nullptr, p->group);
   p->launches = nl;
   p->timed_run = p->timing;
   return rc == 0 ? SD_OK : SD_ECUDA;
@@ -525,7 +528,7 @@ extern "C" int sd_plan_count_ops(sd_plan *p, int64_t *ops) {
   if (nd > 0) {
     unsigned long long *d = nullptr;
     if (cudaMalloc(&d, sizeof(unsigned long long) * nd) != cudaSuccess) return SD_ENOMEM;
-    int rc = sd_k_count_ops(p->d_designs, nd, p->max_n, p->energy->d, d, nullptr);
+    int rc = sd_k_count_ops(p->d_designs, nd, p->max_n, p->energy->d, d, nullptr, p->group);
     bool ok = rc == 0 && cudaMemcpy(h.data(), d, sizeof(unsigned long long) * nd,
                                     cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(d);
@@ -534,6 +537,46 @@ extern "C" int sd_plan_count_ops(sd_plan *p, int64_t *ops) {
   for (size_t k = 0; k < p->items.size(); k++)
     ops[k] = p->items[k].dev_index >= 0 ? (int64_t)h[p->items[k].dev_index] : 0;
   return SD_OK;
+}
+
+extern "C" int sd_plan_set_timing(sd_plan *p, int enable);
+extern "C" int sd_plan_phase_times(const sd_plan *p, float *ms);
+
+extern "C" int sd_plan_set_group(sd_plan *p, int group) {
+  if (!p || !(group == 1 || group == 8 || group == 32)) return SD_EINVAL;
+  p->group = group;
+  return SD_OK;
+}
+
+extern "C" int sd_plan_get_group(const sd_plan *p) { return p ? p->group : SD_EINVAL; }
+
+// Autotuner: run the whole plan once per candidate group size (fill timed with
+// events on the legacy default stream) and keep the fastest.
+extern "C" int sd_plan_autotune(sd_plan *p, float *ms_out) {
+  if (!p) return SD_EINVAL;
+  static const int cand[3] = {1, 8, 32};
+  if (p->hdesigns.empty()) return SD_OK;
+  const bool had = p->timing;
+  int rc = sd_plan_set_timing(p, 1);
+  if (rc != SD_OK) return rc;
+  float best = 0.0f;
+  int best_g = p->group;
+  for (int k = 0; k < 3; k++) {
+    p->group = cand[k];
+    rc = sd_plan_run(p, nullptr);
+    if (rc != SD_OK) break;
+    float ms[3];
+    rc = sd_plan_phase_times(p, ms);
+    if (rc != SD_OK) break;
+    if (ms_out) ms_out[k] = ms[0];
+    if (k == 0 || ms[0] < best) {
+      best = ms[0];
+      best_g = cand[k];
+    }
+  }
+  p->group = best_g;
+  p->timing = had;
+  return rc;
 }
 
 extern "C" int sd_plan_set_timing(sd_plan *p, int enable) {

@@ -19,7 +19,9 @@
 #define SD_MAXOUT 4      // out-edges per state (one per label in a DFA)
 #define SD_MAXIN 8       // in-edges per state (codon trie: at most 6)
 #define SD_RING 32       // diagonals kept for the windowed two-loop tables
+#define SD_WN 49         // inner-table entries per cell slot
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
+#define SD_MAX_NT 12000  // longest mRNA: keeps every table index inside int32
 
 // +infinity and the finiteness threshold of the fixed-point arithmetic.
 // Stored values are either SD_INF or finite with |v| < 2^57 (checked on the
@@ -80,6 +82,11 @@ struct SdDesign {
   uint32_t *ILk;
   int64_t *Q;             // SD_RING*(n+1)*SLOTS*6 closed-interior values per outer type
   uint32_t *Qk;
+  // SD_RING*(n+1)*SLOTS*SD_WN inner tables of each cell (c,d): the best inner
+  // type with one loop-side term folded in, packed as value*8 + type:
+  // [0,16) 1xn mismatch, [16,32) 2x3 mismatch, [32,48) generic mismatch, each
+  // indexed (label into c)*4 + (label out of d); [48] bulge terminal penalty
+  int64_t *W;
   int32_t *cand_cnt;      // N   |C_b|
   const int64_t *cand_off;// N   first entry of C_b
   int32_t *cand_c;        // start states of the retained candidates
@@ -100,10 +107,11 @@ extern "C" {
 #endif
 // events: NULL or four cudaEvent_t recorded before the fill, after the fill,
 // after the exterior pass and after the traceback, on `stream`
+// group: threads per layer pair in the fill (1, 2, 4, 8, 16 or 32)
 int sd_k_run(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-             void *stream, int64_t *launches, void *const *events);
+             void *stream, int64_t *launches, void *const *events, int group);
 int sd_k_count_ops(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                   unsigned long long *d_ops, void *stream);
+                   unsigned long long *d_ops, void *stream, int group);
 int sd_k_clear(const SdDesign *h_designs, const SdDesign *d_designs, int count, void *stream);
 #ifdef __cplusplus
 }

@@ -32,7 +32,6 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int FILL_WARPS = 4;
 constexpr uint32_t KEY_NONE = 0xffffffffu;
 
 __constant__ int c_pair5[6] = {0, 1, 2, 3, 2, 3};
@@ -93,13 +92,8 @@ struct Lat {
   __device__ Lat(const SdDesign &d) : D(d) {}
   __device__ __forceinline__ int layer(int v) const { return __ldg(&D.layer[v]); }
   __device__ __forceinline__ int lstart(int l) const { return __ldg(&D.lstart[l]); }
-  __device__ __forceinline__ int sl(int v, int l) const { return v - lstart(l); }
   __device__ __forceinline__ int64_t slot(int x, int y, int lx, int ly) const {
     return (diag_off(D.n, ly - lx) + lx) * SD_SLOTS + (x - lstart(lx)) * SD_W + (y - lstart(ly));
-  }
-  __device__ __forceinline__ int64_t rslot(int x, int y, int lx, int ly) const {
-    return ((int64_t)((ly - lx) % SD_RING) * (D.n + 1) + lx) * SD_SLOTS + (x - lstart(lx)) * SD_W +
-           (y - lstart(ly));
   }
   // min path cost x -> y; 0 for x == y; +inf without a path
   __device__ __forceinline__ int64_t Hp(int x, int y) const {
@@ -131,10 +125,6 @@ struct Lat {
     for (int k = 0; k < nout(v); k++)
       if (D.out[v * SD_MAXOUT + k].label == lab) return k;
     return -1;
-  }
-  // (first, last) labels of the canonical min-cost path x -> y, x != y
-  __device__ __forceinline__ int hkey(int x, int y) const {
-    return D.Hk[slot(x, y, layer(x), layer(y))];
   }
 };
 
@@ -195,11 +185,96 @@ __device__ int hairpin_seq_e(const SdParams &P, const int32_t *hp_len, int t, ui
     if (COUNT) ops += 2 * ((k) + 1);   \
   } while (0)
 
+// The hot scalar tables, staged in shared memory by every fill block.
+struct SmallTables {
+  int32_t stack[6][6];
+  int32_t mmH[6][16], mmI[6][16], mm1n[6][16], mm23[6][16];
+  int32_t bulge[32], interior[32];
+  int32_t au[6];
+  int32_t ninio, maxninio, mlclosing, mlintern, mlbase;
+};
+
+template <int G>
+__device__ __forceinline__ void seg_lexmin(int64_t &v, uint32_t &k) {
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) {
+    const int64_t v2 = __shfl_xor_sync(FULL, v, o);
+    const uint32_t k2 = __shfl_xor_sync(FULL, k, o);
+    upd(v, k, v2, k2);
+  }
+}
+
+// Design view for the fill: hot pointers in registers, 32-bit index math
+// (sizes are limited to n <= 12000 nucleotides on the host).
+struct Fv {
+  int n;
+  const int32_t *__restrict__ lst;
+  const SdEdge *__restrict__ oe;
+  const SdEdge *__restrict__ ie;
+  const uint8_t *__restrict__ on;
+  const uint8_t *__restrict__ in_;
+  const int64_t *H;
+  const uint8_t *Hk;
+  const int64_t *V;
+  __device__ __forceinline__ int ls(int l) const { return __ldg(lst + l); }
+  __device__ __forceinline__ int w(int l) const { return __ldg(lst + l + 1) - __ldg(lst + l); }
+  __device__ __forceinline__ int doff(int s) const { return (s - 1) * (n + 1) - (((s - 1) * s) >> 1); }
+  // packed slot of (layer lx, slot sx) -> (layer ly, slot sy), ly > lx
+  __device__ __forceinline__ int cs(int lx, int sx, int ly, int sy) const {
+    return (doff(ly - lx) + lx) * SD_SLOTS + sx * SD_W + sy;
+  }
+  __device__ __forceinline__ int rs(int lx, int sx, int ly, int sy) const {
+    return (((ly - lx) & (SD_RING - 1)) * (n + 1) + lx) * SD_SLOTS + sx * SD_W + sy;
+  }
+  // min path cost, 0 on the same state, +inf on another state of the same layer
+  __device__ __forceinline__ int64_t Hh(int lx, int sx, int ly, int sy) const {
+    if (ly == lx) return sx == sy ? 0 : SD_INF;
+    return H[cs(lx, sx, ly, sy)];
+  }
+  __device__ __forceinline__ int nout(int v) const { return on[v]; }
+  __device__ __forceinline__ int nin(int v) const { return in_[v]; }
+  __device__ __forceinline__ SdEdge out(int v, int k) const { return oe[v * SD_MAXOUT + k]; }
+  __device__ __forceinline__ SdEdge in(int v, int k) const { return ie[v * SD_MAXIN + k]; }
+  __device__ __forceinline__ void v6(int idx, int64_t (&vv)[6]) const {
+    const longlong2 *p = reinterpret_cast<const longlong2 *>(V + (int64_t)idx * 6);
+    const longlong2 a = p[0], b = p[1], c = p[2];
+    vv[0] = a.x;
+    vv[1] = a.y;
+    vv[2] = b.x;
+    vv[3] = b.y;
+    vv[4] = c.x;
+    vv[5] = c.y;
+  }
+};
+
+// lexicographic minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
+__device__ __forceinline__ void best_inner(const int64_t (&vv)[6], const int32_t (*tab)[16], int idx,
+                                           int64_t &bv, int &bt) {
+  bv = SD_INF;
+  bt = 7;
+#pragma unroll
+  for (int ti = 0; ti < 6; ti++)
+    if (fin(vv[ti])) {
+      const int64_t v = vv[ti] + fx(tab[c_rev[ti]][idx]);
+      if (v < bv) {
+        bv = v;
+        bt = ti;
+      }
+    }
+}
+
+// one outer type t per call: the running (value, key) minimum of Q_t
+#define FOR_T(body) \
+  do {              \
+    body;           \
+  } while (0)
+
 // ---------------------------------------------------------------------------
-// closed-interior values Q_t(x, y), all outer types t at once: the loop closed
-// by an outer pair of type t whose interior path runs from x (after the 5'
-// nucleotide of the pair) to y (before its 3' nucleotide).  Work item `it`
-// of the layer pair; items are spread over the lanes of the owning warp.
+// closed-interior value Q_t(x, y) for one outer type t: the loop
+// closed by an outer pair of type t whose interior path runs from x (after
+// the 5' nucleotide of the pair) to y (before its 3' nucleotide).  x is slot
+// sx of layer lx, y slot sy of layer ly.  The work items of one layer pair are
+// spread over its G threads:
 //   it 0        hairpin
 //   it 1..31    l1 = 0, l2 = it-1        (stack, right bulges)
 //   it 32..61   l2 = 0, l1 = it-31       (left bulges)
@@ -208,116 +283,125 @@ __device__ int hairpin_seq_e(const SdParams &P, const int32_t *hp_len, int t, ui
 //   it 119..121 2x2, 2x3, 3x2
 //   it 122      generic internal loops through IL
 //   it 123      multiloop
+// Where the loop energy splits into a part that depends on the inner pair and
+// a part that depends on the outer one, the best inner type comes from the
+// inner cell's precomputed table.
 // ---------------------------------------------------------------------------
-constexpr int Q_ITEMS = 124;
+// Item classes {first item, count, lane rotation}: the two heavy classes
+// (1xn and nx1) go first on lanes 0.., bulges fill in, the small classes take
+// the lanes the heavy ones leave free, so lanes of a group carry similar work.
+constexpr int Q_CLASSES = 8;
+__constant__ int c_qclass[Q_CLASSES][3] = {{62, 29, 0}, {91, 28, 0}, {1, 31, 1},   {32, 30, 2},
+                                           {119, 3, 29}, {0, 1, 31}, {122, 1, 30}, {123, 1, 29}};
 
 template <bool COUNT>
-__device__ void q_item(const Lat &G, const SdParams &P, int it, int x, int y, int lx, int ly,
-                       int tmask, int64_t *qv, uint32_t *qk, unsigned long long &ops) {
-  const SdDesign &D = G.D;
+__device__ __forceinline__ void q_item(const Fv &F, const SdDesign &D, const SdParams &P,
+                                       const SmallTables &T, int it, int x, int y, int lx, int sx,
+                                       int ly, int sy, int t, int64_t &qv, uint32_t &qk,
+                                       unsigned long long &ops) {
   const int g = ly - lx;
   if (it == 0) {
     if (g < 3) return;
     if (g == 3 || g == 4 || g == 6) {
       // every interior path, lexicographic label order
       int st[8], kk[8];
-      int64_t cs[8];
+      int64_t cst[8];
       uint32_t labs[8];
       int depth = 0;
       st[0] = x;
       kk[0] = 0;
-      cs[0] = 0;
+      cst[0] = 0;
       labs[0] = 0;
       while (depth >= 0) {
         if (depth == g) {
-          for (int t = 0; t < 6; t++)
-            if ((tmask >> t) & 1) {
-              upd(qv[t], qk[t], fx(hairpin_seq_e(P, D.hp_len, t, labs[g], g)) + cs[g], labs[g]);
-              TERM(g);
-            }
+          const uint32_t lb = labs[g];
+          FOR_T({
+            upd(qv, qk, fx(hairpin_seq_e(P, D.hp_len, t, lb, g)) + cst[g], lb);
+            TERM(g);
+          });
           depth--;
           continue;
         }
         const int v = st[depth];
         const int k = kk[depth]++;
-        if (k >= G.nout(v)) {
+        if (k >= F.nout(v)) {
           depth--;
           continue;
         }
-        const SdEdge e = G.out(v, k);
-        if (depth + 1 == g ? e.other != y : !fin(G.Hp(e.other, y))) continue;
+        const SdEdge e = F.out(v, k);
+        const int le = lx + depth + 1;
+        if (depth + 1 == g ? e.other != y : !fin(F.Hh(le, e.other - F.ls(le), ly, sy))) continue;
         st[depth + 1] = e.other;
-        cs[depth + 1] = cs[depth] + e.cost;
+        cst[depth + 1] = cst[depth] + e.cost;
         labs[depth + 1] = (labs[depth] << 2) | (uint32_t)e.label;
         kk[depth + 1] = 0;
         depth++;
       }
     } else {
-      for (int a = 0; a < G.nout(x); a++) {
-        const SdEdge e1 = G.out(x, a);
-        for (int b = 0; b < G.nin(y); b++) {
-          const SdEdge e2 = G.in(y, b);
-          const int64_t h = G.Hp(e1.other, e2.other);
+      const int l1s = F.ls(lx + 1), l2s = F.ls(ly - 1);
+      const int64_t he = fx(__ldg(&D.hp_len[g]));
+      for (int a = 0; a < F.nout(x); a++) {
+        const SdEdge e1 = F.out(x, a);
+        for (int b = 0; b < F.nin(y); b++) {
+          const SdEdge e2 = F.in(y, b);
+          const int64_t h = F.Hh(lx + 1, e1.other - l1s, ly - 1, e2.other - l2s);
           if (!fin(h)) continue;
-          const int64_t base = e1.cost + e2.cost + h;
+          const int64_t base = e1.cost + e2.cost + h + he;
           const uint32_t key = (uint32_t)(e1.label * 4 + e2.label);
-          for (int t = 0; t < 6; t++)
-            if ((tmask >> t) & 1) {
-              upd(qv[t], qk[t], base + fx(hairpin_generic_e(P, D.hp_len, t, g, e1.label, e2.label)),
-                  key);
-              TERM(3);
-            }
+          FOR_T({
+            upd(qv, qk, base + fx(T.mmH[t][e1.label * 4 + e2.label]), key);
+            TERM(3);
+          });
         }
       }
     }
     return;
   }
-  if (it <= 31) {  // l1 = 0: stack (l2 = 0) and bulges on the 3' side
-    const int l2 = it - 1;
-    if (g - l2 < 5) return;
-    const int ld = ly - l2;
-    for (int d = G.lstart(ld); d < G.lstart(ld + 1); d++) {
+  if (it <= 61) {  // stack and bulges: one side empty
+    const bool right = it <= 31;
+    const int l = right ? it - 1 : it - 31;
+    if (g - l < 5) return;
+    const int lo = right ? ly - l : lx + l;  // layer of the inner state that moves
+    const int wo = F.w(lo);
+    for (int so = 0; so < wo; so++) {
       int64_t h = 0;
-      int hf = 0, hl = 0;
-      if (l2 > 0) {
-        h = G.Hp(d, y);
+      int hk = 0;
+      if (l > 0) {
+        const int q = right ? F.cs(lo, so, ly, sy) : F.cs(lx, sx, lo, so);
+        h = F.H[q];
         if (!fin(h)) continue;
-        const int hk = G.hkey(d, y);
-        hf = hk >> 2;
-        hl = hk & 3;
-      } else if (d != y) {
+        hk = F.Hk[q];
+      } else if (so != sy) {
         continue;
       }
-      for (int ti = 0; ti < 6; ti++) {
-        const int64_t v = G.Vt(x, d, ti);
-        if (!fin(v)) continue;
-        const uint32_t key = tl_key(0, l2, G.sl(x, lx), G.sl(d, ld), ti, 0, 0, hf, hl);
-        for (int t = 0; t < 6; t++)
-          if ((tmask >> t) & 1) {
-            upd(qv[t], qk[t], v + h + fx(twoloop_e(P, t, ti, 0, l2, 0, 0, 0, 0)), key);
+      const int cs = right ? sx : so, ds = right ? so : sy;
+      const uint32_t kb = right ? tl_key(0, l, cs, ds, 0, 0, 0, hk >> 2, hk & 3)
+                                : tl_key(l, 0, cs, ds, 0, hk >> 2, hk & 3, 0, 0);
+      if (l >= 2) {
+        // bulge: bulge[l] + AU(t) + AU(inner); best inner type from the inner table
+        const int rc = right ? F.rs(lx, sx, lo, so) : F.rs(lo, so, ly, sy);
+        const int64_t pk = D.W[(int64_t)rc * SD_WN + 48];
+        if (!fin(pk)) continue;
+        const int64_t b2 = (pk >> 3) + h + fx(T.bulge[l]);
+        const uint32_t key = kb | ((uint32_t)(pk & 7) << 8);
+        FOR_T({
+          upd(qv, qk, b2 + fx(T.au[t]), key);
+          TERM(2);
+        });
+      } else {
+        int64_t vv[6];
+        F.v6(right ? F.cs(lx, sx, lo, so) : F.cs(lo, so, ly, sy), vv);
+        const int64_t e1 = h + fx(l == 1 ? T.bulge[1] : 0);
+#pragma unroll
+        for (int ti = 0; ti < 6; ti++) {
+          if (!fin(vv[ti])) continue;
+          const int s = c_rev[ti];
+          const uint32_t key = kb | ((uint32_t)ti << 8);
+          FOR_T({
+            upd(qv, qk, vv[ti] + e1 + fx(T.stack[t][s]), key);
             TERM(2);
-          }
-      }
-    }
-    return;
-  }
-  if (it <= 61) {  // l2 = 0, l1 >= 1: bulges on the 5' side
-    const int l1 = it - 31;
-    if (g - l1 < 5) return;
-    const int lc = lx + l1;
-    for (int c = G.lstart(lc); c < G.lstart(lc + 1); c++) {
-      const int64_t h = G.Hp(x, c);
-      if (!fin(h)) continue;
-      const int hk = G.hkey(x, c);
-      for (int ti = 0; ti < 6; ti++) {
-        const int64_t v = G.Vt(c, y, ti);
-        if (!fin(v)) continue;
-        const uint32_t key = tl_key(l1, 0, G.sl(c, lc), G.sl(y, ly), ti, hk >> 2, hk & 3, 0, 0);
-        for (int t = 0; t < 6; t++)
-          if ((tmask >> t) & 1) {
-            upd(qv[t], qk[t], v + h + fx(twoloop_e(P, t, ti, l1, 0, 0, 0, 0, 0)), key);
-            TERM(2);
-          }
+          });
+        }
       }
     }
     return;
@@ -325,82 +409,135 @@ __device__ void q_item(const Lat &G, const SdParams &P, int it, int x, int y, in
   if (it <= 90) {  // l1 = 1: 1x1, 1x2, 1xn
     const int l2 = it - 61;
     if (g - 1 - l2 < 5) return;
-    const int ld = ly - l2;
-    for (int a = 0; a < G.nout(x); a++) {
-      const SdEdge ec = G.out(x, a);
-      const int c = ec.other, p = ec.label, cs = G.sl(c, lx + 1);
-      for (int d = G.lstart(ld); d < G.lstart(ld + 1); d++) {
+    const int ld = ly - l2, wd = F.w(ld), lds = F.ls(ld);
+    const int lc = lx + 1, lcs = F.ls(lc);
+    const int ld1s = F.ls(ld + 1), ly1s = F.ls(ly - 1);
+    const int64_t e0 = fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
+    for (int a = 0; a < F.nout(x); a++) {
+      const SdEdge ec = F.out(x, a);
+      const int p = ec.label, cs = ec.other - lcs;
+      for (int ds = 0; ds < wd; ds++) {
+        const int d = lds + ds;
         int64_t vv[6];
-        bool any = false;
-        for (int ti = 0; ti < 6; ti++) {
-          vv[ti] = G.Vt(c, d, ti);
-          any |= fin(vv[ti]);
+        if (l2 <= 2) {
+          F.v6(F.cs(lc, cs, ld, ds), vv);
+          if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
+            continue;
         }
-        if (!any) continue;
-        const int ds = G.sl(d, ld);
-        // right side: first edge out of d, last edge into y, min path between
-        for (int b = 0; b < G.nout(d); b++) {
-          const SdEdge r1 = G.out(d, b);
-          for (int b2 = 0; b2 < G.nin(y); b2++) {
-            const SdEdge r2 = G.in(y, b2);
-            int64_t h;
-            if (l2 == 1) {
-              if (r1.other != y || b2 > 0) continue;
-              h = 0;
-            } else {
-              h = G.Hp(r1.other, r2.other);
+        for (int b = 0; b < F.nout(d); b++) {
+          const SdEdge r1 = F.out(d, b);
+          const int fR = r1.label;
+          if (l2 >= 3) {
+            const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR];
+            if (!fin(pk)) continue;
+            const int64_t wv = pk >> 3;
+            const int wt = (int)(pk & 7);
+            const int64_t base = wv + ec.cost + r1.cost + e0;
+            for (int b2 = 0; b2 < F.nin(y); b2++) {
+              const SdEdge r2 = F.in(y, b2);
+              const int64_t h = F.Hh(ld + 1, r1.other - ld1s, ly - 1, r2.other - ly1s);
               if (!fin(h)) continue;
+              const int lR = r2.label;
+              const uint32_t key = tl_key(1, l2, cs, ds, wt, p, p, fR, lR);
+              const int64_t b3 = base + h + r2.cost;
+              FOR_T({
+                upd(qv, qk, b3 + fx(T.mm1n[t][p * 4 + lR]), key);
+                TERM(5);
+              });
             }
-            const int fR = r1.label, lR = l2 == 1 ? r1.label : r2.label;
-            const int64_t base = ec.cost + r1.cost + (l2 == 1 ? 0 : r2.cost + h);
+          } else if (l2 == 1) {
+            if (r1.other != y) continue;
+            const int64_t base = ec.cost + r1.cost;
+#pragma unroll
             for (int ti = 0; ti < 6; ti++) {
               if (!fin(vv[ti])) continue;
-              const uint32_t key = tl_key(1, l2, cs, ds, ti, p, p, fR, lR);
-              for (int t = 0; t < 6; t++)
-                if ((tmask >> t) & 1) {
-                  upd(qv[t], qk[t], vv[ti] + base + fx(twoloop_e(P, t, ti, 1, l2, p, p, fR, lR)),
-                      key);
+              const int s = c_rev[ti];
+              const uint32_t key = tl_key(1, 1, cs, ds, ti, p, p, fR, fR);
+              FOR_T({
+                upd(qv, qk, vv[ti] + base + fx(P.int11[t][s][p * 4 + fR]), key);
+                TERM(3);
+              });
+            }
+          } else {  // l2 == 2: explicit 2-edge right side
+            const int m = r1.other;
+            for (int b2 = 0; b2 < F.nout(m); b2++) {
+              const SdEdge r2 = F.out(m, b2);
+              if (r2.other != y) continue;
+              const int lR = r2.label;
+              const int64_t base = ec.cost + r1.cost + r2.cost;
+#pragma unroll
+              for (int ti = 0; ti < 6; ti++) {
+                if (!fin(vv[ti])) continue;
+                const int s = c_rev[ti];
+                const uint32_t key = tl_key(1, 2, cs, ds, ti, p, p, fR, lR);
+                FOR_T({
+                  upd(qv, qk, vv[ti] + base + fx(P.int21[t][s][p * 16 + fR * 4 + lR]), key);
                   TERM(4);
-                }
+                });
+              }
             }
           }
         }
       }
     }
+    (void)lds;
     return;
   }
   if (it <= 118) {  // l2 = 1, l1 >= 2: 2x1, nx1
     const int l1 = it - 89;
     if (g - 1 - l1 < 5) return;
-    const int lc = lx + l1;
-    for (int b = 0; b < G.nin(y); b++) {
-      const SdEdge er = G.in(y, b);
-      const int d = er.other, r = er.label, ds = G.sl(d, ly - 1);
-      for (int c = G.lstart(lc); c < G.lstart(lc + 1); c++) {
+    const int lc = lx + l1, wc = F.w(lc), lcs = F.ls(lc);
+    const int ld = ly - 1, lds = F.ls(ld);
+    const int lx1s = F.ls(lx + 1), lc1s = F.ls(lc - 1);
+    const int64_t e0 = fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
+    for (int b = 0; b < F.nin(y); b++) {
+      const SdEdge er = F.in(y, b);
+      const int r = er.label, ds = er.other - lds;
+      for (int cs = 0; cs < wc; cs++) {
+        const int c = lcs + cs;
         int64_t vv[6];
-        bool any = false;
-        for (int ti = 0; ti < 6; ti++) {
-          vv[ti] = G.Vt(c, d, ti);
-          any |= fin(vv[ti]);
+        if (l1 == 2) {
+          F.v6(F.cs(lc, cs, ld, ds), vv);
+          if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
+            continue;
         }
-        if (!any) continue;
-        const int cs = G.sl(c, lc);
-        for (int a = 0; a < G.nout(x); a++) {
-          const SdEdge p1 = G.out(x, a);
-          for (int a2 = 0; a2 < G.nin(c); a2++) {
-            const SdEdge p2 = G.in(c, a2);
-            const int64_t h = G.Hp(p1.other, p2.other);
-            if (!fin(h)) continue;
-            const int64_t base = er.cost + p1.cost + p2.cost + h;
-            for (int ti = 0; ti < 6; ti++) {
-              if (!fin(vv[ti])) continue;
-              const uint32_t key = tl_key(l1, 1, cs, ds, ti, p1.label, p2.label, r, r);
-              for (int t = 0; t < 6; t++)
-                if ((tmask >> t) & 1) {
-                  upd(qv[t], qk[t],
-                      vv[ti] + base + fx(twoloop_e(P, t, ti, l1, 1, p1.label, p2.label, r, r)), key);
+        for (int a2 = 0; a2 < F.nin(c); a2++) {
+          const SdEdge p2 = F.in(c, a2);
+          const int lL = p2.label;
+          if (l1 >= 3) {
+            const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r];
+            if (!fin(pk)) continue;
+            const int64_t wv = pk >> 3;
+            const int wt = (int)(pk & 7);
+            const int64_t base = wv + er.cost + p2.cost + e0;
+            for (int a = 0; a < F.nout(x); a++) {
+              const SdEdge p1 = F.out(x, a);
+              const int64_t h = F.Hh(lx + 1, p1.other - lx1s, lc - 1, p2.other - lc1s);
+              if (!fin(h)) continue;
+              const int fL = p1.label;
+              const uint32_t key = tl_key(l1, 1, cs, ds, wt, fL, lL, r, r);
+              const int64_t b3 = base + h + p1.cost;
+              FOR_T({
+                upd(qv, qk, b3 + fx(T.mm1n[t][fL * 4 + r]), key);
+                TERM(5);
+              });
+            }
+          } else {  // l1 == 2: explicit 2-edge left side
+            for (int a = 0; a < F.nout(x); a++) {
+              const SdEdge p1 = F.out(x, a);
+              if (p1.other != p2.other) continue;
+              const int fL = p1.label;
+              const int64_t base = er.cost + p1.cost + p2.cost;
+#pragma unroll
+              for (int ti = 0; ti < 6; ti++) {
+                if (!fin(vv[ti])) continue;
+                const int s = c_rev[ti];
+                const uint32_t key = tl_key(2, 1, cs, ds, ti, fL, lL, r, r);
+                FOR_T({
+                  upd(qv, qk, vv[ti] + base + fx(P.int21[s][t][r * 16 + fL * 4 + lL]), key);
                   TERM(4);
-                }
+                });
+              }
             }
           }
         }
@@ -413,42 +550,66 @@ __device__ void q_item(const Lat &G, const SdParams &P, int it, int x, int y, in
     const int l1 = cls == 2 ? 3 : 2, l2 = cls == 1 ? 3 : 2;
     if (g - l1 - l2 < 5) return;
     const int lc = lx + l1, ld = ly - l2;
-    for (int c = G.lstart(lc); c < G.lstart(lc + 1); c++)
-      for (int d = G.lstart(ld); d < G.lstart(ld + 1); d++) {
+    const int wc = F.w(lc), wd = F.w(ld), lcs = F.ls(lc), lds = F.ls(ld);
+    const int lx1s = F.ls(lx + 1), lc1s = F.ls(lc - 1), ld1s = F.ls(ld + 1), ly1s = F.ls(ly - 1);
+    for (int cs = 0; cs < wc; cs++)
+      for (int ds = 0; ds < wd; ds++) {
+        const int c = lcs + cs, d = lds + ds;
         int64_t vv[6];
-        bool any = false;
-        for (int ti = 0; ti < 6; ti++) {
-          vv[ti] = G.Vt(c, d, ti);
-          any |= fin(vv[ti]);
+        if (cls == 0) {
+          F.v6(F.cs(lc, cs, ld, ds), vv);
+          if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
+            continue;
         }
-        if (!any) continue;
-        const int cs = G.sl(c, lc), ds = G.sl(d, ld);
-        for (int a = 0; a < G.nout(x); a++) {
-          const SdEdge p1 = G.out(x, a);
-          for (int a2 = 0; a2 < G.nin(c); a2++) {
-            const SdEdge p2 = G.in(c, a2);
-            const int64_t hl = G.Hp(p1.other, p2.other);
-            if (!fin(hl)) continue;
-            for (int b = 0; b < G.nout(d); b++) {
-              const SdEdge r1 = G.out(d, b);
-              for (int b2 = 0; b2 < G.nin(y); b2++) {
-                const SdEdge r2 = G.in(y, b2);
-                const int64_t hr = G.Hp(r1.other, r2.other);
+        for (int a2 = 0; a2 < F.nin(c); a2++) {
+          const SdEdge p2 = F.in(c, a2);
+          for (int b = 0; b < F.nout(d); b++) {
+            const SdEdge r1 = F.out(d, b);
+            // inner part: best inner type for this (lL, fR) (2x3 / 3x2 only)
+            int64_t wv = SD_INF;
+            int wt = 7;
+            if (cls) {
+              const int64_t pk =
+                  D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + p2.label * 4 + r1.label];
+              if (fin(pk)) {
+                wv = pk >> 3;
+                wt = (int)(pk & 7);
+              }
+            }
+            if (cls && !fin(wv)) continue;
+            for (int a = 0; a < F.nout(x); a++) {
+              const SdEdge p1 = F.out(x, a);
+              const int64_t hl = F.Hh(lx + 1, p1.other - lx1s, lc - 1, p2.other - lc1s);
+              if (!fin(hl)) continue;
+              for (int b2 = 0; b2 < F.nin(y); b2++) {
+                const SdEdge r2 = F.in(y, b2);
+                const int64_t hr = F.Hh(ld + 1, r1.other - ld1s, ly - 1, r2.other - ly1s);
                 if (!fin(hr)) continue;
-                const int64_t base = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
-                for (int ti = 0; ti < 6; ti++) {
-                  if (!fin(vv[ti])) continue;
+                const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
+                if (cls) {
                   const uint32_t key =
-                      tl_key(l1, l2, cs, ds, ti, p1.label, p2.label, r1.label, r2.label);
-                  for (int t = 0; t < 6; t++)
-                    if ((tmask >> t) & 1) {
-                      upd(qv[t], qk[t],
-                          vv[ti] + base +
-                              fx(twoloop_e(P, t, ti, l1, l2, p1.label, p2.label, r1.label,
-                                           r2.label)),
+                      tl_key(l1, l2, cs, ds, wt, p1.label, p2.label, r1.label, r2.label);
+                  const int64_t b3 = wv + hc + fx(T.interior[5] + T.ninio);
+                  FOR_T({
+                    upd(qv, qk, b3 + fx(T.mm23[t][p1.label * 4 + r2.label]), key);
+                    TERM(8);
+                  });
+                } else {
+#pragma unroll
+                  for (int ti = 0; ti < 6; ti++) {
+                    if (!fin(vv[ti])) continue;
+                    const int s = c_rev[ti];
+                    const uint32_t key =
+                        tl_key(2, 2, cs, ds, ti, p1.label, p2.label, r1.label, r2.label);
+                    FOR_T({
+                      upd(qv, qk,
+                          vv[ti] + hc +
+                              fx(P.int22[t][s][p1.label * 64 + p2.label * 16 + r1.label * 4 +
+                                               r2.label]),
                           key);
                       TERM(8);
-                    }
+                    });
+                  }
                 }
               }
             }
@@ -459,246 +620,352 @@ __device__ void q_item(const Lat &G, const SdParams &P, int it, int x, int y, in
   }
   if (it == 122) {  // generic internal loops: mismatch edges + IL two spans below
     if (g < 11) return;
-    for (int a = 0; a < G.nout(x); a++) {
-      const SdEdge e1 = G.out(x, a);
-      for (int b = 0; b < G.nin(y); b++) {
-        const SdEdge e2 = G.in(y, b);
-        const int64_t rs = G.rslot(e1.other, e2.other, lx + 1, ly - 1);
-        const int64_t il = D.IL[rs];
+    const int l1s = F.ls(lx + 1), l2s = F.ls(ly - 1);
+    for (int a = 0; a < F.nout(x); a++) {
+      const SdEdge e1 = F.out(x, a);
+      for (int b = 0; b < F.nin(y); b++) {
+        const SdEdge e2 = F.in(y, b);
+        const int r = F.rs(lx + 1, e1.other - l1s, ly - 1, e2.other - l2s);
+        const int64_t il = D.IL[r];
         if (!fin(il)) continue;
-        const uint32_t key = (1u << 25) | D.ILk[rs] | ((uint32_t)e1.label << 6) | (uint32_t)e2.label;
+        const uint32_t key = (1u << 25) | D.ILk[r] | ((uint32_t)e1.label << 6) | (uint32_t)e2.label;
         const int64_t base = il + e1.cost + e2.cost;
-        for (int t = 0; t < 6; t++)
-          if ((tmask >> t) & 1) {
-            upd(qv[t], qk[t], base + fx(P.mmI[t][e1.label * 4 + e2.label]), key);
-            TERM(3);
-          }
+        FOR_T({
+          upd(qv, qk, base + fx(T.mmI[t][e1.label * 4 + e2.label]), key);
+          TERM(3);
+        });
       }
     }
     return;
   }
   // multiloop closed by the pair
   if (g < 10) return;
-  const int64_t s2 = D.S2[G.slot(x, y, lx, ly)];
+  const int64_t s2 = D.S2[F.cs(lx, sx, ly, sy)];
   if (!fin(s2)) return;
-  for (int t = 0; t < 6; t++)
-    if ((tmask >> t) & 1) {
-      upd(qv[t], qk[t], s2 + fx(P.mlclosing + P.mlintern + P.au[t]), KEY_ML);
-      TERM(1);
-    }
+  FOR_T({
+    upd(qv, qk, s2 + fx(T.mlclosing + T.mlintern + T.au[t]), KEY_ML);
+    TERM(1);
+  });
 }
 
+// (l1', l2') pairs of the generic internal loops, l1'+l2' in [2, 26]
+constexpr int IL_PAIRS = 375;
+
 // ---------------------------------------------------------------------------
-// the span kernel: one warp per layer pair (i, i+g)
+// the span kernel: G threads per layer pair (i, i+g).  With G = 1 a warp
+// takes 32 layer pairs of one residue class mod 3 (so its lanes see the same
+// layer types and take the same branches); otherwise consecutive groups take
+// consecutive layer pairs.
 // ---------------------------------------------------------------------------
-template <bool COUNT>
-__global__ void __launch_bounds__(FILL_WARPS * 32) k_fill_span(const SdDesign *__restrict__ designs,
-                                                              const SdParams *__restrict__ Pp, int g,
-                                                              unsigned long long *ops_out) {
+template <int G>
+struct FillShape {
+  static constexpr int threads = G == 1 ? 96 : 128;
+  static constexpr int pairs = threads / G;
+  __device__ static int pair_index(int bx) {
+    if (G == 1) {
+      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+      return bx * 96 + warp + 3 * lane;
+    }
+    return bx * pairs + (int)threadIdx.x / G;
+  }
+};
+
+template <int G, bool COUNT>
+__global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::threads)
+    k_fill_span(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp, int g,
+                unsigned long long *ops_out) {
+  constexpr int NT = FillShape<G>::threads;
+  __shared__ SmallTables T;
+  __shared__ uint16_t s_il[IL_PAIRS];
+  {
+    const int32_t *src[] = {&Pp->stack[0][0], &Pp->mmH[0][0], &Pp->bulge[0], &Pp->au[0],
+                            &Pp->ninio};
+    int32_t *dst[] = {&T.stack[0][0], &T.mmH[0][0], &T.bulge[0], &T.au[0], &T.ninio};
+    const int cnt[] = {36, 4 * 96, 64, 6, 5};
+#pragma unroll
+    for (int q = 0; q < 5; q++)
+      for (int k = threadIdx.x; k < cnt[q]; k += NT) dst[q][k] = src[q][k];
+    for (int k = threadIdx.x; k < 27 * 27; k += NT) {
+      const int l1p = k / 27, l2p = k % 27;
+      if (l1p + l2p < 2 || l1p + l2p > SD_MAXTWO - 4) continue;
+      // rank of (l1p, l2p) among the admissible pairs in row-major order
+      int r = 0;
+      for (int a = 0; a < l1p; a++) r += (SD_MAXTWO - 4 - a + 1) - (a < 2 ? 2 - a : 0);
+      r += l2p - (l1p < 2 ? 2 - l1p : 0);
+      s_il[r] = (uint16_t)(l1p | (l2p << 5));
+    }
+  }
+  __syncthreads();
   unsigned long long ops = 0;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, sub = lane & (G - 1);
   const SdDesign &D = designs[blockIdx.y];
   const SdParams &P = *Pp;
   const int n = D.n;
-  const int i = blockIdx.x * FILL_WARPS + (threadIdx.x >> 5);
-  if (g > n || i > n - g) return;  // uniform per warp
+  const int i = FillShape<G>::pair_index(blockIdx.x);
+  const bool active = g <= n && i <= n - g;
+  if (__all_sync(FULL, !active)) return;
   const int j = i + g;
-  Lat G(D);
-  const int a0 = G.lstart(i), wa = G.lstart(i + 1) - a0;
-  const int b0 = G.lstart(j), wb = G.lstart(j + 1) - b0;
-  const int64_t cell = (diag_off(n, g) + i) * SD_SLOTS;
-  const int64_t rcell = ((int64_t)(g % SD_RING) * (n + 1) + i) * SD_SLOTS;
-  const int64_t mlb = fx(P.mlbase);
+  Fv F;
+  F.n = n;
+  F.lst = D.lstart;
+  F.oe = D.out;
+  F.ie = D.in;
+  F.on = D.out_cnt;
+  F.in_ = D.in_cnt;
+  F.H = D.H;
+  F.Hk = D.Hk;
+  F.V = D.V;
+  int a0 = 0, wa = 0, b0 = 0, wb = 0;
+  if (active) {
+    a0 = F.ls(i);
+    wa = F.ls(i + 1) - a0;
+    b0 = F.ls(j);
+    wb = F.ls(j + 1) - b0;
+  }
+  const int cell = active ? (F.doff(g) + i) * SD_SLOTS : 0;
+  const int rcell = ((g & (SD_RING - 1)) * (n + 1) + i) * SD_SLOTS;
+  const int64_t mlb = fx(T.mlbase);
+  const int js = active ? F.ls(j - 1) : 0;  // first state on layer j-1
+  const int i1s = active ? F.ls(i + 1) : 0;
 
   int64_t Bs[SD_SLOTS], PSs[SD_SLOTS];
-  for (int sa = 0; sa < wa; sa++)
-    for (int sb = 0; sb < wb; sb++) {
-      const int a = a0 + sa, b = b0 + sb, s = sa * SD_W + sb;
-      // gap cell (all lanes, redundant: at most a few in-edges)
-      {
-        int64_t hv = SD_INF;
-        uint32_t hk = KEY_NONE;
-        for (int k = 0; k < G.nin(b); k++) {
-          const SdEdge e = G.in(b, k);
-          const int64_t hp = G.Hp(a, e.other);
-          if (!fin(hp)) continue;
-          const int f = e.other == a ? e.label : (G.hkey(a, e.other) >> 2);
-          upd(hv, hk, hp + e.cost, (uint32_t)(f * 4 + e.label));
-          TERM(1);
+#pragma unroll
+  for (int s = 0; s < SD_SLOTS; s++) {
+    Bs[s] = SD_INF;
+    PSs[s] = SD_INF;
+  }
+#pragma unroll 1
+  for (int s = 0; s < SD_SLOTS; s++) {
+    const int sa = s / SD_W, sb = s % SD_W;
+    const bool ok = active && sa < wa && sb < wb;
+    const int a = a0 + sa, b = b0 + sb;
+    // gap cell (every thread of the group; at most a few in-edges)
+    if (ok) {
+      int64_t hv = SD_INF;
+      uint32_t hk = KEY_NONE;
+      for (int k = 0; k < F.nin(b); k++) {
+        const SdEdge e = F.in(b, k);
+        int64_t hp;
+        int f;
+        if (g == 1) {
+          hp = e.other == a ? 0 : SD_INF;
+          f = e.label;
+        } else {
+          const int q = F.cs(i, sa, j - 1, e.other - js);
+          hp = F.H[q];
+          f = F.Hk[q] >> 2;
         }
-        settle(hv, hk);
-        if (lane == 0) {
-          D.H[cell + s] = hv;
-          D.Hk[cell + s] = (uint8_t)(hk & 15);
+        if (!fin(hp)) continue;
+        upd(hv, hk, hp + e.cost, (uint32_t)(f * 4 + e.label));
+        TERM(1);
+      }
+      settle(hv, hk);
+      if (sub == 0) {
+        D.H[cell + s] = hv;
+        D.Hk[cell + s] = (uint8_t)(hk & 15);
+      }
+    }
+    // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side
+    // mismatch; key fields: slot of c, slot of d, inner type, lL, fR
+    {
+      int64_t iv = SD_INF;
+      uint32_t ik = KEY_NONE;
+      if (ok && g >= 7) {
+        const int no = F.nout(a), ni = F.nin(b);
+        for (int q = sub; q < no * ni; q += G) {
+          const int k2 = q % ni, k1 = q / ni;
+          const SdEdge e1 = F.out(a, k1), e2 = F.in(b, k2);
+          const int cs = e1.other - i1s, ds = e2.other - js;
+          const int64_t pk =
+              D.W[(int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label];
+          if (!fin(pk)) continue;
+          const uint32_t key = ((uint32_t)cs << 13) | ((uint32_t)ds << 11) |
+                               ((uint32_t)(pk & 7) << 8) | ((uint32_t)e1.label << 4) |
+                               ((uint32_t)e2.label << 2);
+          upd(iv, ik, (pk >> 3) + e1.cost + e2.cost, key);
+          TERM(3);
         }
       }
-      // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side
-      // mismatch; key fields: slot of c, slot of d, inner type, lL, fR
-      {
-        int64_t iv = SD_INF;
-        uint32_t ik = KEY_NONE;
-        if (g >= 7) {
-          const int no = G.nout(a), ni = G.nin(b);
-          for (int q = lane; q < no * ni * 6; q += 32) {
-            const int ti = q % 6, k2 = (q / 6) % ni, k1 = q / (6 * ni);
-            const SdEdge e1 = G.out(a, k1), e2 = G.in(b, k2);
-            const int64_t v = G.Vt(e1.other, e2.other, ti);
-            if (!fin(v)) continue;
-            const uint32_t key = ((uint32_t)G.sl(e1.other, i + 1) << 13) |
-                                 ((uint32_t)G.sl(e2.other, j - 1) << 11) | ((uint32_t)ti << 8) |
-                                 ((uint32_t)e1.label << 4) | ((uint32_t)e2.label << 2);
-            upd(iv, ik, v + e1.cost + e2.cost + fx(P.mmI[c_rev[ti]][e2.label * 4 + e1.label]), key);
-            TERM(3);
-          }
-          warp_lexmin(iv, ik);
-        }
-        settle(iv, ik);
-        if (lane == 0) {
-          D.Ihat[rcell + s] = iv;
-          D.Ihk[rcell + s] = ik;
-        }
+      seg_lexmin<G>(iv, ik);
+      settle(iv, ik);
+      if (ok && sub == 0) {
+        D.Ihat[rcell + s] = iv;
+        D.Ihk[rcell + s] = ik;
       }
-      // IL: generic internal loops l1 = l1'+2, l2 = l2'+2 around (a,b)
-      {
-        int64_t lv = SD_INF;
-        uint32_t lk = KEY_NONE;
-        if (g >= 9) {
-          for (int q = lane; q < 27 * 27; q += 32) {
-            const int l1p = q / 27, l2p = q % 27;
-            if (l1p + l2p < 2 || l1p + l2p > SD_MAXTWO - 4) continue;  // 2x2, 2x3, 3x2: own classes
-            const int lc = i + l1p, ld = j - l2p;
-            if (ld - lc < 7) continue;
-            const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
-            const int64_t e = fx(P.interior[l1p + l2p + 4] + min(P.maxninio, P.ninio * dd));
-            const uint32_t kl = ((uint32_t)(l1p + l2p + 4) << 20) | ((uint32_t)(l1p + 2) << 15);
-            for (int c = G.lstart(lc); c < G.lstart(lc + 1); c++) {
-              const int64_t hl = G.Hp(a, c);
-              if (!fin(hl)) continue;
-              for (int d = G.lstart(ld); d < G.lstart(ld + 1); d++) {
-                const int64_t hr = G.Hp(d, b);
-                if (!fin(hr)) continue;
-                const int64_t rs = G.rslot(c, d, lc, ld);
-                const int64_t v = D.Ihat[rs];
-                if (!fin(v)) continue;
-                upd(lv, lk, hl + v + hr + e, kl | D.Ihk[rs]);
-                TERM(3);
-              }
+    }
+    // IL: generic internal loops l1 = l1'+2, l2 = l2'+2 around (a,b)
+    {
+      int64_t lv = SD_INF;
+      uint32_t lk = KEY_NONE;
+      if (ok && g >= 9) {
+        for (int q = sub; q < IL_PAIRS; q += G) {
+          const int pr = s_il[q];
+          const int l1p = pr & 31, l2p = pr >> 5;
+          const int lc = i + l1p, ld = j - l2p;
+          if (ld - lc < 7) continue;
+          const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
+          const int64_t e = fx(T.interior[l1p + l2p + 4] + min(T.maxninio, T.ninio * dd));
+          const uint32_t kl = ((uint32_t)(l1p + l2p + 4) << 20) | ((uint32_t)(l1p + 2) << 15);
+          const int wc = F.w(lc), wd = F.w(ld);
+          for (int cs = 0; cs < wc; cs++) {
+            const int64_t hl = F.Hh(i, sa, lc, cs);
+            if (!fin(hl)) continue;
+            for (int ds = 0; ds < wd; ds++) {
+              const int64_t hr = F.Hh(ld, ds, j, sb);
+              if (!fin(hr)) continue;
+              const int r = F.rs(lc, cs, ld, ds);
+              const int64_t v = D.Ihat[r];
+              if (!fin(v)) continue;
+              upd(lv, lk, hl + v + hr + e, kl | D.Ihk[r]);
+              TERM(3);
             }
           }
-          warp_lexmin(lv, lk);
-        }
-        settle(lv, lk);
-        if (lane == 0) {
-          D.IL[rcell + s] = lv;
-          D.ILk[rcell + s] = lk;
         }
       }
-      // typed closed values (lane t computes type t) and Eq. (branch)
+      seg_lexmin<G>(lv, lk);
+      settle(lv, lk);
+      if (ok && sub == 0) {
+        D.IL[rcell + s] = lv;
+        D.ILk[rcell + s] = lk;
+      }
+    }
+    // typed closed values (every thread of the group) and Eq. (branch)
+    int64_t vv[6];
+    {
       int64_t B = SD_INF;
       uint32_t Bk = KEY_NONE;
-      {
-        int64_t vv = SD_INF;
+#pragma unroll
+      for (int t = 0; t < 6; t++) {
+        int64_t v = SD_INF;
         uint32_t vk = KEY_NONE;
-        if (g >= 5 && lane < 6) {
-          const int t = lane;
-          const int k1 = G.out_with_label(a, c_pair5[t]);
-          if (k1 >= 0) {
-            const SdEdge e1 = G.out(a, k1);
-            for (int k2 = 0; k2 < G.nin(b); k2++) {
-              const SdEdge e2 = G.in(b, k2);
+        if (ok && g >= 5) {
+          for (int k1 = 0; k1 < F.nout(a); k1++) {
+            const SdEdge e1 = F.out(a, k1);
+            if (e1.label != c_pair5[t]) continue;
+            for (int k2 = 0; k2 < F.nin(b); k2++) {
+              const SdEdge e2 = F.in(b, k2);
               if (e2.label != c_pair3[t]) continue;
-              const int64_t rs = G.rslot(e1.other, e2.other, i + 1, j - 1) * 6 + t;
-              const int64_t q = D.Q[rs];
+              const int r = F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t;
+              const int64_t q = D.Q[r];
               if (!fin(q)) continue;
-              upd(vv, vk, q + e1.cost + e2.cost, ((uint32_t)k2 << 27) | D.Qk[rs]);
+              upd(v, vk, q + e1.cost + e2.cost, ((uint32_t)k2 << 27) | D.Qk[r]);
               TERM(2);
             }
           }
         }
-        settle(vv, vk);
-        if (lane < 6) {
-          D.V[(cell + s) * 6 + lane] = vv;
-          D.Vk[(cell + s) * 6 + lane] = vk;
-          if (fin(vv)) {
-            B = vv + fx(P.mlintern + P.au[lane]);
-            Bk = lane;
-            TERM(1);
-          }
+        settle(v, vk);
+        vv[t] = v;
+        if (ok && sub == t % G) {
+          D.V[(int64_t)(cell + s) * 6 + t] = v;
+          D.Vk[(int64_t)(cell + s) * 6 + t] = vk;
         }
-        warp_lexmin(B, Bk);
-        settle(B, Bk);
-        if (lane == 0) {
-          D.Bv[cell + s] = B;
-          D.Bk[cell + s] = (uint8_t)(Bk & 7);
+        if (fin(v)) {
+          upd(B, Bk, v + fx(T.mlintern + T.au[t]), (uint32_t)t);
+          TERM(1);
         }
       }
-      // Eq. (sparse2): edge extensions, then splits at retained candidates
-      int64_t s2 = SD_INF;
-      uint32_t s2k = KEY_NONE;
-      {
-        for (int k = 0; k < G.nin(b); k++) {
-          const SdEdge e = G.in(b, k);
-          if (G.layer(e.other) <= i) continue;
-          const int64_t v = G.S2(a, e.other);
+      settle(B, Bk);
+      if (ok && sub == 0) {
+        D.Bv[cell + s] = B;
+        D.Bk[cell + s] = (uint8_t)(Bk & 7);
+      }
+      Bs[s] = B;
+    }
+    // inner tables of this cell for the two-loops that will enclose it
+    if (ok) {
+      const int im = D.in_mask[a], om = D.out_mask[b];
+      int64_t *Wc = D.W + (int64_t)(rcell + s) * SD_WN;
+      for (int q = sub; q < SD_WN; q += G) {
+        int64_t bv = SD_INF;
+        int bt = 7;
+        if (g >= 5) {
+          if (q < 48) {
+            const int tab = q >> 4, li = (q >> 2) & 3, lo = q & 3;
+            if (((im >> li) & 1) && ((om >> lo) & 1))
+              best_inner(vv, tab == 0 ? T.mm1n : tab == 1 ? T.mm23 : T.mmI, lo * 4 + li, bv, bt);
+          } else {
+#pragma unroll
+            for (int ti = 0; ti < 6; ti++)
+              if (fin(vv[ti])) {
+                const int64_t v = vv[ti] + fx(T.au[c_rev[ti]]);
+                if (v < bv) {
+                  bv = v;
+                  bt = ti;
+                }
+              }
+          }
+        }
+        Wc[q] = fin(bv) ? bv * 8 + bt : SD_INF;
+      }
+    }
+  }
+  // Eq. (sparse2) for every slot: edge extensions, then splits at retained
+  // candidates (the group splits the candidate list)
+#pragma unroll 1
+  for (int s = 0; s < SD_SLOTS; s++) {
+    const int sa = s / SD_W, sb = s % SD_W;
+    const bool ok = active && sa < wa && sb < wb;
+    const int a = a0 + sa, b = b0 + sb;
+    int64_t s2 = SD_INF;
+    uint32_t s2k = KEY_NONE;
+    if (ok) {
+      if (g >= 2 && sub == 0)
+        for (int k = 0; k < F.nin(b); k++) {
+          const SdEdge e = F.in(b, k);
+          const int64_t v = D.S2[F.cs(i, sa, j - 1, e.other - js)];
           if (!fin(v)) continue;
           upd(s2, s2k, v + e.cost + mlb, (uint32_t)k);
           TERM(2);
         }
-        const int cnt = D.cand_cnt[b];
-        const int64_t off = D.cand_off[b];
-        for (int k = lane; k < cnt; k += 32) {
-          const int c = D.cand_c[off + k];
-          const int lc = G.layer(c);
-          if (lc <= i) break;  // entries are in decreasing layer order
-          const int64_t v = D.S1[G.slot(a, c, i, lc)];
-          if (!fin(v)) continue;
-          upd(s2, s2k, v + D.cand_B[off + k], KEY_SPLIT | (uint32_t)c);
-          TERM(1);
-        }
-        warp_lexmin(s2, s2k);
-        settle(s2, s2k);
-        if (lane == 0) {
-          D.S2[cell + s] = s2;
-          D.S2k[cell + s] = s2k;
-        }
+      const int cnt = D.cand_cnt[b];
+      const int64_t off = D.cand_off[b];
+      for (int k = sub; k < cnt; k += G) {
+        const int c = D.cand_c[off + k];
+        const int lc = __ldg(&D.layer[c]);
+        if (lc <= i) break;  // entries are in decreasing layer order
+        const int64_t v = D.S1[F.cs(i, sa, lc, c - F.ls(lc))];
+        if (!fin(v)) continue;
+        upd(s2, s2k, v + D.cand_B[off + k], KEY_SPLIT | (uint32_t)c);
+        TERM(1);
       }
+    }
+    seg_lexmin<G>(s2, s2k);
+    settle(s2, s2k);
+    if (ok && sub == 0) {
+      D.S2[cell + s] = s2;
+      D.S2k[cell + s] = s2k;
       // P_S (Eq. partitionable with S) and S1 = min(B, P_S); key classes:
       // 0 direct branch, 1 left peel, 2 right peel, 3 two-branch value
-      {
-        int64_t ps = s2;
-        uint32_t psk = 3u << 4;
-        if (!fin(ps)) psk = KEY_NONE;
-        for (int k = 0; k < G.nout(a); k++) {
-          const SdEdge e = G.out(a, k);
-          if (G.layer(e.other) >= j) continue;
-          const int64_t v = G.S1(e.other, b);
+      int64_t ps = s2;
+      uint32_t psk = fin(s2) ? (3u << 4) : KEY_NONE;
+      if (g >= 2) {
+        for (int k = 0; k < F.nout(a); k++) {
+          const SdEdge e = F.out(a, k);
+          const int64_t v = D.S1[F.cs(i + 1, e.other - i1s, j, sb)];
           if (!fin(v)) continue;
           upd(ps, psk, v + e.cost + mlb, (1u << 4) | (uint32_t)k);
           TERM(2);
         }
-        for (int k = 0; k < G.nin(b); k++) {
-          const SdEdge e = G.in(b, k);
-          if (G.layer(e.other) <= i) continue;
-          const int64_t v = G.S1(a, e.other);
+        for (int k = 0; k < F.nin(b); k++) {
+          const SdEdge e = F.in(b, k);
+          const int64_t v = D.S1[F.cs(i, sa, j - 1, e.other - js)];
           if (!fin(v)) continue;
           upd(ps, psk, v + e.cost + mlb, (2u << 4) | (uint32_t)k);
           TERM(2);
         }
-        settle(ps, psk);
-        int64_t s1 = ps;
-        uint32_t s1k = psk;
-        if (fin(B)) upd(s1, s1k, B, 0u);
-        if (lane == 0) {
-          D.S1[cell + s] = s1;
-          D.S1k[cell + s] = s1k;
-        }
-        Bs[s] = B;
-        PSs[s] = ps;
       }
+      settle(ps, psk);
+      int64_t s1 = ps;
+      uint32_t s1k = psk;
+      if (fin(Bs[s])) upd(s1, s1k, Bs[s], 0u);
+      D.S1[cell + s] = s1;
+      D.S1k[cell + s] = s1k;
+      PSs[s] = ps;
     }
+  }
   // candidate appends (Eq. candidates); the list of b is in decreasing layer
   // order and states of one layer are appended in descending id order
-  if (lane == 0)
+  if (active && sub == 0)
     for (int sb = 0; sb < wb; sb++) {
       const int b = b0 + sb;
       int cnt = D.cand_cnt[b];
@@ -714,31 +981,38 @@ __global__ void __launch_bounds__(FILL_WARPS * 32) k_fill_span(const SdDesign *_
       D.cand_cnt[b] = cnt;
     }
   // closed-interior values for the pairs two spans up
-  for (int sa = 0; sa < wa; sa++)
-    for (int sb = 0; sb < wb; sb++) {
-      const int x = a0 + sa, y = b0 + sb, s = sa * SD_W + sb;
-      int tmask = 0;
+#pragma unroll 1
+  for (int s = 0; s < SD_SLOTS; s++) {
+    const int sa = s / SD_W, sb = s % SD_W;
+    const bool ok = active && sa < wa && sb < wb;
+    const int x = a0 + sa, y = b0 + sb;
+    int tmask = 0;
+    if (ok) {
+      const int im = D.in_mask[x], om = D.out_mask[y];
+#pragma unroll
       for (int t = 0; t < 6; t++)
-        if (((D.in_mask[x] >> c_pair5[t]) & 1) && ((D.out_mask[y] >> c_pair3[t]) & 1))
-          tmask |= 1 << t;
-      int64_t qv[6];
-      uint32_t qk[6];
-      for (int t = 0; t < 6; t++) {
-        qv[t] = SD_INF;
-        qk[t] = KEY_NONE;
-      }
-      if (tmask)
-        for (int it = lane; it < Q_ITEMS; it += 32)
-          q_item<COUNT>(G, P, it, x, y, i, j, tmask, qv, qk, ops);
-      for (int t = 0; t < 6; t++) {
-        if ((tmask >> t) & 1) warp_lexmin(qv[t], qk[t]);
-        settle(qv[t], qk[t]);
-        if (lane == t) {
-          D.Q[(rcell + s) * 6 + t] = qv[t];
-          D.Qk[(rcell + s) * 6 + t] = qk[t];
+        if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tmask |= 1 << t;
+    }
+    // one outer type at a time (the types of a layer pair are the same for
+    // all threads of its group); types that cannot close (x, y) stay +inf
+#pragma unroll 1
+    for (int t = 0; t < 6; t++) {
+      int64_t qv = SD_INF;
+      uint32_t qk = KEY_NONE;
+      if ((tmask >> t) & 1)
+        for (int cl = 0; cl < Q_CLASSES; cl++) {
+          const int st = c_qclass[cl][0], cnt = c_qclass[cl][1], rot = c_qclass[cl][2] % G;
+          for (int k = (sub - rot + G) % G; k < cnt; k += G)
+            q_item<COUNT>(F, D, P, T, st + k, x, y, i, sa, j, sb, t, qv, qk, ops);
         }
+      if (__any_sync(FULL, (tmask >> t) & 1)) seg_lexmin<G>(qv, qk);
+      settle(qv, qk);
+      if (ok && sub == 0) {
+        D.Q[(int64_t)(rcell + s) * 6 + t] = qv;
+        D.Qk[(int64_t)(rcell + s) * 6 + t] = qk;
       }
     }
+  }
   if (COUNT) {
     for (int o = 16; o > 0; o >>= 1) ops += __shfl_xor_sync(FULL, ops, o);
     if (lane == 0) atomicAdd(&ops_out[blockIdx.y], ops);
@@ -1192,14 +1466,27 @@ __global__ void k_count(const SdDesign *__restrict__ designs, unsigned long long
   atomicAdd(&out[blockIdx.y * 4 + 2], rc + z);
 }
 
-template <bool COUNT>
-void launch_fill(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                 cudaStream_t st, unsigned long long *d_ops) {
+template <int G, bool COUNT>
+void launch_fill_g(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
+                   cudaStream_t st, unsigned long long *d_ops) {
+  constexpr int per_block = G == 1 ? 96 : FillShape<G>::pairs;
   for (int g = 1; g <= max_n; g++) {
     const int cells = max_n - g + 1;
-    dim3 grid((cells + FILL_WARPS - 1) / FILL_WARPS, count);
-    k_fill_span<COUNT><<<grid, FILL_WARPS * 32, 0, st>>>(d_designs, d_params, g, d_ops);
+    dim3 grid((cells + per_block - 1) / per_block, count);
+    k_fill_span<G, COUNT><<<grid, FillShape<G>::threads, 0, st>>>(d_designs, d_params, g, d_ops);
   }
+}
+
+template <bool COUNT>
+int launch_fill(int G, const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
+                cudaStream_t st, unsigned long long *d_ops) {
+  switch (G) {
+    case 1: launch_fill_g<1, COUNT>(d_designs, count, max_n, d_params, st, d_ops); break;
+    case 8: launch_fill_g<8, COUNT>(d_designs, count, max_n, d_params, st, d_ops); break;
+    case 32: launch_fill_g<32, COUNT>(d_designs, count, max_n, d_params, st, d_ops); break;
+    default: return -1;
+  }
+  return 0;
 }
 
 }  // namespace
@@ -1215,17 +1502,18 @@ extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, 
 // Counting pass: the same fill with algorithmic-work counters (INT32 slots
 // per design, see TERM); the result tables are identical to sd_k_run's.
 extern "C" int sd_k_count_ops(const SdDesign *d_designs, int count, int max_n,
-                              const SdParams *d_params, unsigned long long *d_ops, void *stream) {
+                              const SdParams *d_params, unsigned long long *d_ops, void *stream,
+                              int group) {
   cudaStream_t st = (cudaStream_t)stream;
   if (count <= 0) return 0;
   if (cudaMemsetAsync(d_ops, 0, sizeof(unsigned long long) * count, st) != cudaSuccess) return -1;
   k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
-  launch_fill<true>(d_designs, count, max_n, d_params, st, d_ops);
+  if (launch_fill<true>(group, d_designs, count, max_n, d_params, st, d_ops)) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 extern "C" int sd_k_run(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                        void *stream, int64_t *launches, void *const *events) {
+                        void *stream, int64_t *launches, void *const *events, int group) {
   cudaStream_t st = (cudaStream_t)stream;
   if (count <= 0) {
     if (launches) *launches = 0;
@@ -1233,7 +1521,7 @@ extern "C" int sd_k_run(const SdDesign *d_designs, int count, int max_n, const S
   }
   k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
   if (events) cudaEventRecord((cudaEvent_t)events[0], st);
-  launch_fill<false>(d_designs, count, max_n, d_params, st, nullptr);
+  if (launch_fill<false>(group, d_designs, count, max_n, d_params, st, nullptr)) return -1;
   if (events) cudaEventRecord((cudaEvent_t)events[1], st);
   k_exterior<<<count, 256, 0, st>>>(d_designs, d_params);
   if (events) cudaEventRecord((cudaEvent_t)events[2], st);

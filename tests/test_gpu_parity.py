@@ -189,3 +189,16 @@ def test_full_size_design_properties(sd, E1, par1, A, lam):
     r = sd.sd_design(E1, prot, w, lam)
     _design_properties(P, prot, w, lam, r)
     assert 0 < r["Z"] <= r["finite_direct"]
+
+
+@pytest.mark.parametrize("group", [1, 32])
+def test_every_group_size_gives_the_oracle_tables(sd, E1, par1, group):
+    """The fill's threads-per-layer-pair choice changes speed, never results."""
+    prot = inputs.random_protein(35, 31)
+    w = inputs.random_codon_weights(31)
+    o = oracle.run(par1, prot, w, 4.0)
+    plan = sd.Plan(E1, [prot], w, [4.0])
+    plan.group = group
+    plan.run()
+    compare_tables(plan, 0, o)
+    compare_design(plan.results()[0], o, 4.0)
