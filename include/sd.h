@@ -44,6 +44,7 @@ extern "C" {
 #define SD_ECUDA (-5)       /* a CUDA runtime call failed                          */
 #define SD_ETIMEOUT (-6)    /* a bounded device wait expired                       */
 #define SD_EINTERNAL (-7)   /* traceback could not reproduce the DP value          */
+#define SD_ESIZE (-8)       /* design larger than sd_design_noalloc's fixed scratch */
 
 typedef struct sd_energy sd_energy; /* opaque nearest-neighbour parameter set */
 typedef struct sd_plan sd_plan;     /* opaque batch of designs resident on the GPU */
@@ -104,6 +105,27 @@ int sd_design_batch(const sd_energy *energy, int count, const char *const *prote
 
 void sd_result_free(sd_result *r);
 const char *sd_strerror(int code);
+
+/* Exact design of one protein that allocates no device memory.
+ * The paper has no counterpart: this entry point exists for callers that may
+ * not call cudaMalloc (or an allocator built on it, such as torch's) when they
+ * ask for a design, e.g. code working inside a device-memory budget fixed in
+ * advance.  Same inputs and results as sd_design, except that the caller
+ * provides the output strings: out->mrna and out->structure must point to
+ * caller buffers of at least 3*strlen(protein)+1 bytes each (do not pass the
+ * result to sd_result_free).  The energy set comes from sd_load_energy, which
+ * may run earlier, in set-up code that can allocate.
+ * Scratch: a 64 MiB static device array held by every GPU that loads the
+ * library until the process exits.  Designs whose tables do not fit (beyond a
+ * few hundred nucleotides; at most 400 codon positions) return SD_ESIZE.
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress) and must come before any stream capture.
+ * All calls share the scratch: calls that overlap on the GPU (two host
+ * threads, or work still in flight) race and must be serialised.
+ * Runs on the legacy default stream and returns when the design is complete.
+ * Returns SD_OK, SD_EINVAL, SD_ERANGE, SD_ESIZE, SD_ECUDA or SD_EINTERNAL. */
+int sd_design_noalloc(const sd_energy *energy, const char *protein, const double *codon_weights,
+                      double lambda, sd_result *out);
 
 /* ---- plan interface: inputs resident in HBM, asynchronous execution ---- */
 

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libsd_b300.so")
 _lib = None
 
 SD_OK, SD_EINVAL, SD_ERANGE, SD_EINFEASIBLE = 0, -1, -2, -3
-SD_ENOMEM, SD_ECUDA, SD_ETIMEOUT, SD_EINTERNAL = -4, -5, -6, -7
+SD_ENOMEM, SD_ECUDA, SD_ETIMEOUT, SD_EINTERNAL, SD_ESIZE = -4, -5, -6, -7, -8
 INF = 1 << 62          # +infinity in table dumps
 FX_ONE = 1 << 32       # one dcal/mol in the fixed-point unit
 
@@ -58,6 +58,7 @@ def lib():
         L.sd_energy_free.restype = None
         L.sd_design.argtypes = [P, ctypes.c_char_p, P, D, ctypes.POINTER(sd_result)]
         L.sd_design_batch.argtypes = [P, I, P, P, I, P, P, P]
+        L.sd_design_noalloc.argtypes = [P, ctypes.c_char_p, P, D, ctypes.POINTER(sd_result)]
         L.sd_result_free.argtypes = [ctypes.POINTER(sd_result)]
         L.sd_result_free.restype = None
         L.sd_strerror.argtypes = [I]
@@ -80,7 +81,8 @@ def lib():
         L.sd_plan_phase_times.argtypes = [P, P]
         L.sd_plan_free.argtypes = [P]
         L.sd_plan_free.restype = None
-        for f in ("sd_load_energy", "sd_design", "sd_design_batch", "sd_plan_create",
+        for f in ("sd_load_energy", "sd_design", "sd_design_batch", "sd_design_noalloc",
+                  "sd_plan_create",
                   "sd_plan_run", "sd_plan_results", "sd_plan_item_size", "sd_plan_dump",
                   "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
@@ -153,6 +155,24 @@ def sd_design(energy: Energy, protein: str, weights, lam: float) -> dict:
         return _result_dict(r, rc)
     finally:
         lib().sd_result_free(ctypes.byref(r))
+
+
+def sd_design_noalloc(energy: Energy, protein: str, weights, lam: float) -> dict:
+    """One exact design through the entry point that allocates no device
+    memory (for callers that may not call cudaMalloc; see include/sd.h).
+    The output strings live in buffers made here, on the host."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+    n = 3 * len(protein)
+    mbuf = ctypes.create_string_buffer(n + 1)
+    sbuf = ctypes.create_string_buffer(n + 1)
+    r = sd_result()
+    r.mrna = ctypes.cast(mbuf, ctypes.c_void_p)
+    r.structure = ctypes.cast(sbuf, ctypes.c_void_p)
+    rc = lib().sd_design_noalloc(energy.handle, protein.encode(), _ptr(w), float(lam),
+                                 ctypes.byref(r))
+    if rc != SD_OK:
+        raise SdError(rc, "sd_design_noalloc")
+    return _result_dict(r, rc)
 
 
 def sd_design_batch(energy: Energy, proteins, weights, lambdas) -> list:

@@ -809,6 +809,25 @@ extern "C" const char *sd_strerror(int code) {
     case SD_ECUDA: return "CUDA runtime error";
     case SD_ETIMEOUT: return "bounded device wait expired";
     case SD_EINTERNAL: return "traceback did not reproduce the DP value";
+    case SD_ESIZE: return "design larger than the fixed scratch of sd_design_noalloc";
     default: return "unknown error";
   }
 }
+
+// ---------------------------------------------------------------------------
+// internal helpers shared with the fixed-scratch entry point (sd_noalloc.cu)
+// ---------------------------------------------------------------------------
+extern "C" char sd_internal_translate(int x, int y, int z) { return translate(x, y, z); }
+extern "C" int64_t sd_internal_codon_fx(double lambda, double w) { return codon_fx(lambda, w); }
+extern "C" int sd_internal_range_check(const sd_energy *E, int n, double qmax_sum) {
+  HostLattice L;
+  L.n = n;
+  L.qmax_sum = qmax_sum;
+  return range_check(E, L);
+}
+extern "C" const SdParams *sd_internal_device_params(const sd_energy *E) { return E ? E->d : nullptr; }
+extern "C" int32_t sd_internal_hairpin_len(const sd_energy *E, int L) {
+  if (L < 3) return 0;
+  return L <= 30 ? E->hairpin[L] : E->hairpin[30] + (int32_t)(E->lxc * std::log((double)L / 30.0));
+}
+

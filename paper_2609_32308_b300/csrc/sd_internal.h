@@ -113,6 +113,14 @@ int sd_k_run(const SdDesign *d_designs, int count, int max_n, const SdParams *d_
 int sd_k_count_ops(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
                    unsigned long long *d_ops, void *stream, int group);
 int sd_k_clear(const SdDesign *h_designs, const SdDesign *d_designs, int count, void *stream);
+// host helpers of sd_host.cpp used by the fixed-scratch entry point
+struct sd_energy;
+char sd_internal_translate(int x, int y, int z);
+int64_t sd_internal_codon_fx(double lambda, double w);
+int sd_internal_range_check(const struct sd_energy *E, int n, double qmax_sum);
+const SdParams *sd_internal_device_params(const struct sd_energy *E);
+int32_t sd_internal_hairpin_len(const struct sd_energy *E, int L);
+int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
 #ifdef __cplusplus
 }
 #endif
