@@ -346,7 +346,7 @@ struct sd_plan {
   int max_n = 0;
   int64_t launches = 0;
   cudaStream_t last_stream = nullptr;
-  int group = 8;  // threads per layer pair in the fill
+  int group = 32;  // threads per layer pair in the fill
   bool timing = false;
   bool timed_run = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
