@@ -164,6 +164,11 @@ int sd_plan_set_group(sd_plan *plan, int group);
 int sd_plan_get_group(const sd_plan *plan);
 int sd_plan_autotune(sd_plan *plan, float *ms3);
 
+/* Capture the whole run (fill, exterior pass, traceback: one launch per span)
+ * into a CUDA graph on the next sd_plan_run and replay the graph on later runs
+ * (re-captured when the group size or timing changes).  Off by default. */
+int sd_plan_set_graph(sd_plan *plan, int enable);
+
 /* Number of kernel launches one sd_plan_run enqueues. */
 int64_t sd_plan_launches(const sd_plan *plan);
 

@@ -76,6 +76,7 @@ def lib():
         L.sd_plan_set_timing.argtypes = [P, I]
         L.sd_plan_count_ops.argtypes = [P, P]
         L.sd_plan_set_group.argtypes = [P, I]
+        L.sd_plan_set_graph.argtypes = [P, I]
         L.sd_plan_get_group.argtypes = [P]
         L.sd_plan_autotune.argtypes = [P, P]
         L.sd_plan_phase_times.argtypes = [P, P]
@@ -86,7 +87,7 @@ def lib():
                   "sd_plan_run", "sd_plan_results", "sd_plan_item_size", "sd_plan_dump",
                   "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
-                  "sd_plan_autotune"):
+                  "sd_plan_autotune", "sd_plan_set_graph"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -235,6 +236,12 @@ class Plan:
         rc = lib().sd_plan_set_group(self.handle, int(g))
         if rc != SD_OK:
             raise SdError(rc, "sd_plan_set_group")
+
+    def set_graph(self, enable: bool = True):
+        """Replay the whole run as one CUDA graph (captured on the next run)."""
+        rc = lib().sd_plan_set_graph(self.handle, int(bool(enable)))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_set_graph")
 
     def autotune(self):
         """Pick the fastest group size; returns {group: fill ms}."""

@@ -347,6 +347,15 @@ struct sd_plan {
   int64_t launches = 0;
   cudaStream_t last_stream = nullptr;
   int group = 32;  // threads per layer pair in the fill
+  std::vector<int> ns;            // lengths in device order (non-increasing)
+  std::vector<int32_t> cpre_host; // prefix sums of ns + 1
+  int32_t *d_cpre = nullptr;
+  // CUDA graph of one whole run (captured on first use when enabled)
+  bool use_graph = false;
+  bool graph_timed = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t graph_launches = 0;
   bool timing = false;
   bool timed_run = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -469,14 +478,30 @@ extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *co
     if (it.status == SD_OK && it.L.n > SD_MAX_NT) it.status = SD_EINVAL;
     if (it.status == SD_OK) it.status = range_check(energy, it.L);
     if (it.status != SD_OK) continue;
-    it.dev_index = (int)p->hdesigns.size();
     SdDesign d{};
     total += carve(nullptr, it.L, d);
-    p->hdesigns.push_back(d);
     p->max_n = std::max(p->max_n, it.L.n);
   }
   if (item_status)
     for (int k = 0; k < count; k++) item_status[k] = p->items[k].status;
+  // device order: longest design first (the span work queue relies on the
+  // designs still running at span g being a prefix of this order)
+  {
+    std::vector<int> order;
+    for (int k = 0; k < count; k++)
+      if (p->items[k].status == SD_OK) order.push_back(k);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return p->items[x].L.n > p->items[y].L.n; });
+    p->hdesigns.resize(order.size());
+    p->ns.resize(order.size());
+    std::vector<int32_t> cpre(order.size() + 1, 0);
+    for (size_t r = 0; r < order.size(); r++) {
+      p->items[order[r]].dev_index = (int)r;
+      p->ns[r] = p->items[order[r]].L.n;
+      cpre[r + 1] = cpre[r] + p->ns[r] + 1;
+    }
+    p->cpre_host = cpre;
+  }
   if (!p->hdesigns.empty()) {
     if (cudaMalloc(&p->arena, total) != cudaSuccess) {
       cudaGetLastError();
@@ -499,6 +524,9 @@ extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *co
     }
     if (cudaMalloc(&p->d_designs, sizeof(SdDesign) * p->hdesigns.size()) != cudaSuccess ||
         cudaMemcpy(p->d_designs, p->hdesigns.data(), sizeof(SdDesign) * p->hdesigns.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMalloc(&p->d_cpre, sizeof(int32_t) * p->cpre_host.size()) != cudaSuccess ||
+        cudaMemcpy(p->d_cpre, p->cpre_host.data(), sizeof(int32_t) * p->cpre_host.size(),
                    cudaMemcpyHostToDevice) != cudaSuccess) {
       sd_plan_free(p);
       return SD_ECUDA;
@@ -514,11 +542,55 @@ extern "C" int sd_plan_run(sd_plan *p, void *stream) {
   if (p->hdesigns.empty()) return SD_OK;
   int64_t nl = 0;
   void *ev[4] = {p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
-  int rc = sd_k_run(p->d_designs, (int)p->hdesigns.size(), p->max_n, p->energy->d, stream, &nl,
+  const int nd = (int)p->hdesigns.size();
+  if (p->use_graph) {
+    if (p->gexec && p->graph_timed != p->timing) {
+      cudaGraphExecDestroy(p->gexec);
+      p->gexec = nullptr;
+    }
+    if (!p->gexec) {
+      if (!p->cap_stream &&
+          cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return SD_ECUDA;
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+        return SD_ECUDA;
+      int rc = sd_k_run(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, p->cap_stream,
+                        &nl, p->timing ? ev : nullptr, p->group);
+      cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
+      if (rc != 0 || ce != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return SD_ECUDA;
+      }
+      ce = cudaGraphInstantiate(&p->gexec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ce != cudaSuccess) {
+        p->gexec = nullptr;
+        return SD_ECUDA;
+      }
+      p->graph_timed = p->timing;
+      p->graph_launches = nl;
+    }
+    p->launches = p->graph_launches;
+    p->timed_run = p->timing;
+    return cudaGraphLaunch(p->gexec, (cudaStream_t)stream) == cudaSuccess ? SD_OK : SD_ECUDA;
+  }
+  int rc = sd_k_run(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, stream, &nl,
                     p->timing ? ev : nullptr, p->group);
   p->launches = nl;
   p->timed_run = p->timing;
   return rc == 0 ? SD_OK : SD_ECUDA;
+}
+
+extern "C" int sd_plan_set_graph(sd_plan *p, int enable) {
+  if (!p) return SD_EINVAL;
+  if (!enable && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  p->use_graph = enable != 0;
+  return SD_OK;
 }
 
 extern "C" int sd_plan_count_ops(sd_plan *p, int64_t *ops) {
@@ -528,7 +600,8 @@ extern "C" int sd_plan_count_ops(sd_plan *p, int64_t *ops) {
   if (nd > 0) {
     unsigned long long *d = nullptr;
     if (cudaMalloc(&d, sizeof(unsigned long long) * nd) != cudaSuccess) return SD_ENOMEM;
-    int rc = sd_k_count_ops(p->d_designs, nd, p->max_n, p->energy->d, d, nullptr, p->group);
+    int rc = sd_k_count_ops(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, d, nullptr,
+                            p->group);
     bool ok = rc == 0 && cudaMemcpy(h.data(), d, sizeof(unsigned long long) * nd,
                                     cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(d);
@@ -544,6 +617,10 @@ extern "C" int sd_plan_phase_times(const sd_plan *p, float *ms);
 
 extern "C" int sd_plan_set_group(sd_plan *p, int group) {
   if (!p || !(group == 1 || group == 8 || group == 32)) return SD_EINVAL;
+  if (group != p->group && p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
   p->group = group;
   return SD_OK;
 }
@@ -762,6 +839,9 @@ extern "C" void sd_plan_free(sd_plan *p) {
   if (!p) return;
   if (p->arena) cudaFree(p->arena);
   if (p->d_designs) cudaFree(p->d_designs);
+  if (p->d_cpre) cudaFree(p->d_cpre);
+  if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (int k = 0; k < 4; k++)
     if (p->ev[k]) cudaEventDestroy(p->ev[k]);
   delete p;

@@ -105,13 +105,16 @@ struct SdDesign {
 #ifdef __cplusplus
 extern "C" {
 #endif
+// Designs in device order must have non-increasing n (ns[d] = designs[d].n);
+// d_cpre[d] = sum over d' < d of (ns[d'] + 1), count + 1 entries on the device.
 // events: NULL or four cudaEvent_t recorded before the fill, after the fill,
-// after the exterior pass and after the traceback, on `stream`
-// group: threads per layer pair in the fill (1, 2, 4, 8, 16 or 32)
-int sd_k_run(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-             void *stream, int64_t *launches, void *const *events, int group);
-int sd_k_count_ops(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                   unsigned long long *d_ops, void *stream, int group);
+// after the exterior pass and after the traceback, on `stream`.
+// group: threads per layer pair in the fill (1, 8 or 32).
+int sd_k_run(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+             const SdParams *d_params, void *stream, int64_t *launches, void *const *events,
+             int group);
+int sd_k_count_ops(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+                   const SdParams *d_params, unsigned long long *d_ops, void *stream, int group);
 int sd_k_clear(const SdDesign *h_designs, const SdDesign *d_designs, int count, void *stream);
 // host helpers of sd_host.cpp used by the fixed-scratch entry point
 struct sd_energy;

@@ -673,6 +673,7 @@ struct FillShape {
 template <int G, bool COUNT>
 __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::threads)
     k_fill_span(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp, int g,
+                int nact, int items, const int32_t *__restrict__ cpre,
                 unsigned long long *ops_out) {
   constexpr int NT = FillShape<G>::threads;
   __shared__ SmallTables T;
@@ -698,11 +699,25 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
   __syncthreads();
   unsigned long long ops = 0;
   const int lane = threadIdx.x & 31, sub = lane & (G - 1);
-  const SdDesign &D = designs[blockIdx.y];
+  // work queue of the span: the layer pairs of the nact designs still running
+  // (designs sorted by length, longest first), design d owning items
+  // [cpre[d] - d*g, cpre[d+1] - (d+1)*g)
+  const int q = FillShape<G>::pair_index(blockIdx.x);
+  int dsel = 0;
+  if (q < items) {
+    int lo = 0, hi = nact - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (__ldg(&cpre[mid]) - mid * g <= q) lo = mid;
+      else hi = mid - 1;
+    }
+    dsel = lo;
+  }
+  const SdDesign &D = designs[dsel];
   const SdParams &P = *Pp;
   const int n = D.n;
-  const int i = FillShape<G>::pair_index(blockIdx.x);
-  const bool active = g <= n && i <= n - g;
+  const int i = q - (__ldg(&cpre[dsel]) - dsel * g);
+  const bool active = q < items && g <= n && i >= 0 && i <= n - g;
   if (__all_sync(FULL, !active)) return;
   const int j = i + g;
   Fv F;
@@ -1013,10 +1028,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
       }
     }
   }
-  if (COUNT) {
-    for (int o = 16; o > 0; o >>= 1) ops += __shfl_xor_sync(FULL, ops, o);
-    if (lane == 0) atomicAdd(&ops_out[blockIdx.y], ops);
-  }
+  if (COUNT && active && ops) atomicAdd(&ops_out[dsel], ops);
 }
 
 // ---------------------------------------------------------------------------
@@ -1466,24 +1478,36 @@ __global__ void k_count(const SdDesign *__restrict__ designs, unsigned long long
   atomicAdd(&out[blockIdx.y * 4 + 2], rc + z);
 }
 
+// One launch per span over the span's work queue.  ns: lengths of the
+// designs in device order (non-increasing); cpre: their prefix sums of n+1.
 template <int G, bool COUNT>
-void launch_fill_g(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                   cudaStream_t st, unsigned long long *d_ops) {
+void launch_fill_g(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+                   const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
   constexpr int per_block = G == 1 ? 96 : FillShape<G>::pairs;
+  int nact = count;
+  int64_t cp = 0;
+  for (int d = 0; d < count; d++) cp += ns[d] + 1;
+  const int max_n = count > 0 ? ns[0] : 0;
   for (int g = 1; g <= max_n; g++) {
-    const int cells = max_n - g + 1;
-    dim3 grid((cells + per_block - 1) / per_block, count);
-    k_fill_span<G, COUNT><<<grid, FillShape<G>::threads, 0, st>>>(d_designs, d_params, g, d_ops);
+    while (nact > 0 && ns[nact - 1] < g) {
+      nact--;
+      cp -= ns[nact] + 1;
+    }
+    const int64_t items = cp - (int64_t)nact * g;
+    if (items <= 0) break;
+    dim3 grid((unsigned)((items + per_block - 1) / per_block));
+    k_fill_span<G, COUNT><<<grid, FillShape<G>::threads, 0, st>>>(d_designs, d_params, g, nact,
+                                                                  (int)items, d_cpre, d_ops);
   }
 }
 
 template <bool COUNT>
-int launch_fill(int G, const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                cudaStream_t st, unsigned long long *d_ops) {
+int launch_fill(int G, const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+                const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
   switch (G) {
-    case 1: launch_fill_g<1, COUNT>(d_designs, count, max_n, d_params, st, d_ops); break;
-    case 8: launch_fill_g<8, COUNT>(d_designs, count, max_n, d_params, st, d_ops); break;
-    case 32: launch_fill_g<32, COUNT>(d_designs, count, max_n, d_params, st, d_ops); break;
+    case 1: launch_fill_g<1, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
+    case 8: launch_fill_g<8, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
+    case 32: launch_fill_g<32, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
     default: return -1;
   }
   return 0;
@@ -1501,19 +1525,20 @@ extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, 
 
 // Counting pass: the same fill with algorithmic-work counters (INT32 slots
 // per design, see TERM); the result tables are identical to sd_k_run's.
-extern "C" int sd_k_count_ops(const SdDesign *d_designs, int count, int max_n,
-                              const SdParams *d_params, unsigned long long *d_ops, void *stream,
-                              int group) {
+extern "C" int sd_k_count_ops(const SdDesign *d_designs, int count, const int *ns,
+                              const int32_t *d_cpre, const SdParams *d_params,
+                              unsigned long long *d_ops, void *stream, int group) {
   cudaStream_t st = (cudaStream_t)stream;
   if (count <= 0) return 0;
   if (cudaMemsetAsync(d_ops, 0, sizeof(unsigned long long) * count, st) != cudaSuccess) return -1;
   k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
-  if (launch_fill<true>(group, d_designs, count, max_n, d_params, st, d_ops)) return -1;
+  if (launch_fill<true>(group, d_designs, count, ns, d_cpre, d_params, st, d_ops)) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-extern "C" int sd_k_run(const SdDesign *d_designs, int count, int max_n, const SdParams *d_params,
-                        void *stream, int64_t *launches, void *const *events, int group) {
+extern "C" int sd_k_run(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+                        const SdParams *d_params, void *stream, int64_t *launches,
+                        void *const *events, int group) {
   cudaStream_t st = (cudaStream_t)stream;
   if (count <= 0) {
     if (launches) *launches = 0;
@@ -1521,12 +1546,12 @@ extern "C" int sd_k_run(const SdDesign *d_designs, int count, int max_n, const S
   }
   k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
   if (events) cudaEventRecord((cudaEvent_t)events[0], st);
-  if (launch_fill<false>(group, d_designs, count, max_n, d_params, st, nullptr)) return -1;
+  if (launch_fill<false>(group, d_designs, count, ns, d_cpre, d_params, st, nullptr)) return -1;
   if (events) cudaEventRecord((cudaEvent_t)events[1], st);
   k_exterior<<<count, 256, 0, st>>>(d_designs, d_params);
   if (events) cudaEventRecord((cudaEvent_t)events[2], st);
   k_traceback<<<count, 128, 0, st>>>(d_designs, d_params);
   if (events) cudaEventRecord((cudaEvent_t)events[3], st);
-  if (launches) *launches = (int64_t)max_n + 3;
+  if (launches) *launches = (int64_t)ns[0] + 3;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -190,6 +190,7 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   const size_t ring = (size_t)SD_RING * (n + 1) * SD_SLOTS;
   *rec = (SdDesign *)take(sizeof(SdDesign));
   *counts = (int64_t *)take(4 * sizeof(int64_t));
+  take(2 * sizeof(int32_t));  // prefix sums of the one-design work queue (after counts)
   d.n = (int)n;
   d.N = (int)N;
   d.ncell = ncell;
@@ -278,7 +279,12 @@ extern "C" int sd_design_noalloc(const sd_energy *energy, const char *protein,
       !h2d((void *)d.cand_off, L.cand_off, N * 8) || !h2d(rec, &d, sizeof(SdDesign)))
     return SD_ECUDA;
   int64_t launches = 0;
-  if (sd_k_run(rec, 1, L.n, sd_internal_device_params(energy), nullptr, &launches, nullptr, 32))
+  int32_t *cpre = (int32_t *)((char *)counts + 256);  // the 2-int block carved after counts
+  const int32_t cpre_h[2] = {0, (int32_t)n + 1};
+  const int ns[1] = {(int)n};
+  if (!h2d(cpre, cpre_h, sizeof(cpre_h))) return SD_ECUDA;
+  if (sd_k_run(rec, 1, ns, cpre, sd_internal_device_params(energy), nullptr, &launches, nullptr,
+               32))
     return SD_ECUDA;
   if (sd_k_count(rec, 1, counts, nullptr)) return SD_ECUDA;
   int64_t tb[4], ext0 = 0, cnt[4];

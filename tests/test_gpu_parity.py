@@ -202,3 +202,21 @@ def test_every_group_size_gives_the_oracle_tables(sd, E1, par1, group):
     plan.run()
     compare_tables(plan, 0, o)
     compare_design(plan.results()[0], o, 4.0)
+
+
+def test_graph_replay_of_a_mixed_batch(sd, E1, par1):
+    """The span work queue (longest design first) and the captured CUDA graph
+    reproduce the oracle's designs for a batch of uneven lengths, on two
+    replays in a row."""
+    lengths = [30, 7, 45, 12, 45, 3]
+    batch = inputs.protein_batch(lengths, seed=99)
+    prots = [b[0] for b in batch]
+    ws = np.stack([b[1] for b in batch])
+    lams = [b[2] for b in batch]
+    plan = sd.Plan(E1, prots, ws, lams)
+    plan.set_graph(True)
+    for _ in range(2):
+        plan.run()
+        res = plan.results()
+        for (p, w, lam), r in zip(batch, res):
+            compare_design(r, oracle.run(par1, p, w, lam), lam)
