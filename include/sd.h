@@ -193,6 +193,54 @@ int sd_plan_edges(const sd_plan *plan, int item, int32_t *from, int32_t *to, int
                   int64_t *cost);
 void sd_plan_free(sd_plan *plan);
 
+/* ---- retention-count predictor (presizes candidate lists; not in the paper:
+ *      the paper retains candidates by the exact test B < P_S of Sec. 4.1,
+ *      which stays the only rule deciding what is kept) ---- */
+
+#define SD_PRED_FEATURES 32 /* input channels per codon position */
+#define SD_PRED_BANDS 8     /* outputs: span bands 5-7, 8-15, ..., 256-511, >= 512 */
+typedef struct sd_predictor sd_predictor;
+
+/* A 1-D convolutional network (4 convolutions of width 5, 32 -> 128 -> 128 ->
+ * 128 -> 8 channels, ReLU between) with BF16 weights and FP32 accumulation on
+ * the current device.  sd_pred_create draws the weights from a seed. */
+int sd_pred_create(uint64_t seed, sd_predictor **out);
+void sd_pred_free(sd_predictor *p);
+int64_t sd_pred_num_params(void);
+/* FP32 master parameters, layer by layer: W[5][cin][cout] then bias[cout]. */
+int sd_pred_get_params(const sd_predictor *p, float *params);
+int sd_pred_set_params(sd_predictor *p, const float *params);
+/* Features of one protein: strlen(protein) * SD_PRED_FEATURES floats (host). */
+int sd_pred_features(const char *protein, const double *codon_weights, double lambda,
+                     float *feat);
+/* Forward pass of B sequences padded to L positions: feats [B][L][32],
+ * lengths[B], out [B][L][8] = predicted log1p(counts) (host arrays). */
+int sd_pred_forward(sd_predictor *p, int B, int L, const float *feats, const int *lengths,
+                    float *out);
+/* Mean squared error against targets [B][L][8] over the valid positions and
+ * its gradient w.r.t. every parameter (grads may be NULL). */
+int sd_pred_gradients(sd_predictor *p, int B, int L, const float *feats, const float *targets,
+                      const int *lengths, float *grads, float *loss);
+/* One Adam step (beta 0.9 / 0.999) on that loss. */
+int sd_pred_train_step(sd_predictor *p, int B, int L, const float *feats, const float *targets,
+                       const int *lengths, float lr, float *loss);
+/* Training labels from an exact run: counts [A][8] of the retained
+ * candidates of one plan item by codon of the right endpoint and span band. */
+int sd_plan_retention(const sd_plan *plan, int item, int32_t *counts);
+
+/* A plan whose candidate lists get the room the predictor expects (margin x
+ * the predicted count of their codon, plus 8, at most the worst case) instead
+ * of the worst case.  Results are identical to sd_plan_create's: a list that
+ * outgrows its room is detected on the device, and sd_plan_results then gives
+ * the affected designs worst-case room and repeats the run (counted in
+ * sd_result.regrows).  Runs the predictor's forward pass (synchronous). */
+int sd_plan_create_predicted(const sd_energy *energy, sd_predictor *pred, double margin, int count,
+                             const char *const *proteins, const double *codon_weights,
+                             int weights_shared, const double *lambdas, sd_plan **out,
+                             int *item_status);
+/* Candidate-list entries reserved by a plan (all items). */
+int64_t sd_plan_candidate_room(const sd_plan *plan);
+
 #ifdef __cplusplus
 }
 #endif

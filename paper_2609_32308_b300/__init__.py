@@ -77,6 +77,21 @@ def lib():
         L.sd_plan_count_ops.argtypes = [P, P]
         L.sd_plan_set_group.argtypes = [P, I]
         L.sd_plan_set_graph.argtypes = [P, I]
+        L.sd_plan_retention.argtypes = [P, I, P]
+        L.sd_plan_candidate_room.argtypes = [P]
+        L.sd_plan_candidate_room.restype = ctypes.c_int64
+        L.sd_plan_create_predicted.argtypes = [P, P, D, I, P, P, I, P, ctypes.POINTER(P), P]
+        L.sd_pred_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
+        L.sd_pred_free.argtypes = [P]
+        L.sd_pred_free.restype = None
+        L.sd_pred_num_params.argtypes = []
+        L.sd_pred_num_params.restype = ctypes.c_int64
+        L.sd_pred_get_params.argtypes = [P, P]
+        L.sd_pred_set_params.argtypes = [P, P]
+        L.sd_pred_features.argtypes = [ctypes.c_char_p, P, D, P]
+        L.sd_pred_forward.argtypes = [P, I, I, P, P, P]
+        L.sd_pred_gradients.argtypes = [P, I, I, P, P, P, P, P]
+        L.sd_pred_train_step.argtypes = [P, I, I, P, P, P, ctypes.c_float, P]
         L.sd_plan_get_group.argtypes = [P]
         L.sd_plan_autotune.argtypes = [P, P]
         L.sd_plan_phase_times.argtypes = [P, P]
@@ -87,7 +102,10 @@ def lib():
                   "sd_plan_run", "sd_plan_results", "sd_plan_item_size", "sd_plan_dump",
                   "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
-                  "sd_plan_autotune", "sd_plan_set_graph"):
+                  "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention",
+                  "sd_plan_create_predicted", "sd_pred_create", "sd_pred_get_params",
+                  "sd_pred_set_params", "sd_pred_features", "sd_pred_forward",
+                  "sd_pred_gradients", "sd_pred_train_step"):
             getattr(L, f).restype = I
         _lib = L
     return _lib
@@ -199,7 +217,10 @@ def sd_design_batch(energy: Energy, proteins, weights, lambdas) -> list:
 class Plan:
     """A batch of designs resident on the GPU (sd_plan_* calls)."""
 
-    def __init__(self, energy: Energy, proteins, weights, lambdas):
+    def __init__(self, energy: Energy, proteins, weights, lambdas, predictor=None,
+                 margin: float = 2.0):
+        """predictor: a Predictor to presize the candidate lists
+        (sd_plan_create_predicted), or None for worst-case room."""
         self.energy = energy
         self.count = len(proteins)
         w, shared = _weights(weights, self.count)
@@ -208,8 +229,13 @@ class Plan:
         arr = (ctypes.c_char_p * self.count)(*self._keep)
         self.item_status = np.zeros(self.count, dtype=np.int32)
         h = ctypes.c_void_p()
-        rc = lib().sd_plan_create(energy.handle, self.count, arr, _ptr(w), shared, _ptr(lam),
-                                  ctypes.byref(h), _ptr(self.item_status))
+        if predictor is None:
+            rc = lib().sd_plan_create(energy.handle, self.count, arr, _ptr(w), shared, _ptr(lam),
+                                      ctypes.byref(h), _ptr(self.item_status))
+        else:
+            rc = lib().sd_plan_create_predicted(energy.handle, predictor.handle, float(margin),
+                                                self.count, arr, _ptr(w), shared, _ptr(lam),
+                                                ctypes.byref(h), _ptr(self.item_status))
         if rc != SD_OK:
             raise SdError(rc, "sd_plan_create")
         self.handle = h
@@ -287,6 +313,19 @@ class Plan:
             for k in range(self.count):
                 lib().sd_result_free(ctypes.byref(outs[k]))
 
+    def retention(self, item: int) -> np.ndarray:
+        """Retained candidates of one item by (codon, span band), shape (A, 8)."""
+        A = len(self._keep[item]) if item < len(self._keep) else 0
+        out = np.zeros((max(A, 1), 8), dtype=np.int32)
+        rc = lib().sd_plan_retention(self.handle, item, _ptr(out))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_retention")
+        return out[:A]
+
+    @property
+    def candidate_room(self) -> int:
+        return int(lib().sd_plan_candidate_room(self.handle))
+
     def size(self, item: int):
         n, N, E = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
         rc = lib().sd_plan_item_size(self.handle, item, ctypes.byref(n), ctypes.byref(N),
@@ -330,3 +369,79 @@ class Plan:
 
 def sd_plan_create(energy, proteins, weights, lambdas) -> Plan:
     return Plan(energy, proteins, weights, lambdas)
+
+
+class Predictor:
+    """Retention-count predictor (sd_pred_*): a 1-D conv net whose forward,
+    backward and Adam steps run in the library's BF16/FP32 kernels."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        rc = lib().sd_pred_create(int(seed), ctypes.byref(h))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_create")
+        self.handle = h
+        self.nparams = int(lib().sd_pred_num_params())
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, dtype=np.float32)
+        rc = lib().sd_pred_get_params(self.handle, _ptr(out))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_get_params")
+        return out
+
+    def set_params(self, p) -> None:
+        p = np.ascontiguousarray(p, dtype=np.float32).reshape(self.nparams)
+        rc = lib().sd_pred_set_params(self.handle, _ptr(p))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_set_params")
+
+    @staticmethod
+    def features(protein: str, weights, lam: float) -> np.ndarray:
+        w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+        out = np.zeros((max(len(protein), 1), 32), dtype=np.float32)
+        rc = lib().sd_pred_features(protein.encode(), _ptr(w), float(lam), _ptr(out))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_features")
+        return out[:len(protein)]
+
+    def forward(self, feats: np.ndarray, lengths) -> np.ndarray:
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        B, L, _ = f.shape
+        ln = np.ascontiguousarray(lengths, dtype=np.int32)
+        out = np.zeros((B, L, 8), dtype=np.float32)
+        rc = lib().sd_pred_forward(self.handle, B, L, _ptr(f), _ptr(ln), _ptr(out))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_forward")
+        return out
+
+    def gradients(self, feats, targets, lengths):
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        B, L, _ = f.shape
+        ln = np.ascontiguousarray(lengths, dtype=np.int32)
+        g = np.zeros(self.nparams, dtype=np.float32)
+        loss = ctypes.c_float()
+        rc = lib().sd_pred_gradients(self.handle, B, L, _ptr(f), _ptr(t), _ptr(ln), _ptr(g),
+                                     ctypes.byref(loss))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_gradients")
+        return float(loss.value), g
+
+    def train_step(self, feats, targets, lengths, lr: float) -> float:
+        f = np.ascontiguousarray(feats, dtype=np.float32)
+        t = np.ascontiguousarray(targets, dtype=np.float32)
+        B, L, _ = f.shape
+        ln = np.ascontiguousarray(lengths, dtype=np.int32)
+        loss = ctypes.c_float()
+        rc = lib().sd_pred_train_step(self.handle, B, L, _ptr(f), _ptr(t), _ptr(ln),
+                                      float(lr), ctypes.byref(loss))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_pred_train_step")
+        return float(loss.value)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sd_pred_free(self.handle)
+            self.handle = None
+

@@ -187,7 +187,14 @@ struct HostLattice {
   std::vector<int32_t> e_from, e_to, e_label;  // (from, label) order
   std::vector<int64_t> e_cost;
   double qmax_sum = 0.0;  // sum over codon positions of the largest codon cost (FP64)
+  std::vector<int32_t> caps;  // room of each candidate list (empty: worst case)
 };
+
+// worst-case room of C_b: every state at least five layers before b
+int32_t worst_room(const HostLattice &L, int v) { return L.lstart[std::max(0, L.layer[v] - 4)]; }
+int32_t room(const HostLattice &L, int v) {
+  return L.caps.empty() ? worst_room(L, v) : std::min(L.caps[v], worst_room(L, v));
+}
 
 int64_t codon_fx(double lambda, double w) {
   const double lam100 = 100.0 * lambda;
@@ -334,6 +341,8 @@ struct PlanItem {
   int status = SD_OK;
   int dev_index = -1;  // position in the device design array
   SdDesign d{};        // device pointers (host copy of the struct)
+  int regrows = 0;     // runs repeated because a presized candidate list overflowed
+  int32_t *own_cand = nullptr;  // worst-case candidate room allocated by a regrow
 };
 
 struct sd_plan {
@@ -380,7 +389,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   const int64_t n = L.n, N = L.N;
   const int64_t ncell = n * (n + 1) / 2;
   int64_t cap = 0;
-  for (int v = 0; v < N; v++) cap += L.lstart[std::max(0, L.layer[v] - 4)];
+  for (int v = 0; v < N; v++) cap += room(L, v);
   d.n = (int)n;
   d.N = (int)N;
   d.ncell = ncell;
@@ -413,6 +422,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.W = c.take<int64_t>(ring * SD_WN);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
+  d.cand_cap = L.caps.empty() ? nullptr : c.take<int32_t>(N);
   d.cand_c = c.take<int32_t>(std::max<int64_t>(cap, 1));
   d.cand_B = c.take<int64_t>(std::max<int64_t>(cap, 1));
   d.Ext = c.take<int64_t>(N);
@@ -435,8 +445,10 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
   int64_t acc = 0;
   for (int v = 0; v < N; v++) {
     off[v] = acc;
-    acc += L.lstart[std::max(0, L.layer[v] - 4)];
+    acc += room(L, v);
   }
+  std::vector<int32_t> rooms(N);
+  for (int v = 0; v < N; v++) rooms[v] = room(L, v);
   auto cp = [](const void *dst, const void *src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice) ==
                              cudaSuccess;
@@ -446,15 +458,82 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
             cp(d.out_cnt, L.out_cnt.data(), N) &&
             cp(d.in, L.in.data(), L.in.size() * sizeof(SdEdge)) && cp(d.in_cnt, L.in_cnt.data(), N) &&
             cp(d.in_mask, L.in_mask.data(), N) && cp(d.out_mask, L.out_mask.data(), N) &&
-            cp(d.hp_len, hp.data(), (n + 1) * 4) && cp(d.cand_off, off.data(), N * 8);
+            cp(d.hp_len, hp.data(), (n + 1) * 4) && cp(d.cand_off, off.data(), N * 8) &&
+            (!d.cand_cap || cp(d.cand_cap, rooms.data(), N * 4));
   return ok ? SD_OK : SD_ECUDA;
 }
 
 }  // namespace
 
+namespace {
+int plan_create(const sd_energy *energy, const sd_predictor *pred, double margin, int count,
+                const char *const *proteins, const double *codon_weights, int weights_shared,
+                const double *lambdas, sd_plan **out, int *item_status);
+}
+
 extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *const *proteins,
                               const double *codon_weights, int weights_shared,
                               const double *lambdas, sd_plan **out, int *item_status) {
+  return plan_create(energy, nullptr, 0.0, count, proteins, codon_weights, weights_shared, lambdas,
+                     out, item_status);
+}
+
+extern "C" int sd_plan_create_predicted(const sd_energy *energy, sd_predictor *pred, double margin,
+                                        int count, const char *const *proteins,
+                                        const double *codon_weights, int weights_shared,
+                                        const double *lambdas, sd_plan **out, int *item_status) {
+  if (!pred || !(margin > 0.0)) return SD_EINVAL;
+  return plan_create(energy, pred, margin, count, proteins, codon_weights, weights_shared, lambdas,
+                     out, item_status);
+}
+
+namespace {
+// Room of every candidate list from the predictor: the predicted retained
+// candidates of codon k (summed over span bands) times `margin`, plus a few,
+// for every state whose layer lies in codon k (never above the worst case).
+int presize(sd_predictor *pred, double margin, std::vector<PlanItem> &items) {
+  std::vector<int> idx;
+  int Lmax = 1;
+  for (size_t k = 0; k < items.size(); k++)
+    if (items[k].status == SD_OK && !items[k].protein.empty()) {
+      idx.push_back((int)k);
+      Lmax = std::max(Lmax, (int)items[k].protein.size());
+    }
+  if (idx.empty()) return SD_OK;
+  const int B = (int)idx.size();
+  std::vector<float> feats((size_t)B * Lmax * SD_PRED_FEATURES, 0.f), y((size_t)B * Lmax * 8);
+  std::vector<int> lens(B);
+  for (int b = 0; b < B; b++) {
+    const PlanItem &it = items[idx[b]];
+    lens[b] = (int)it.protein.size();
+    int rc = sd_pred_features(it.protein.c_str(), it.w, it.lambda,
+                              feats.data() + (size_t)b * Lmax * SD_PRED_FEATURES);
+    if (rc != SD_OK) return rc;
+  }
+  int rc = sd_pred_forward(pred, B, Lmax, feats.data(), lens.data(), y.data());
+  if (rc != SD_OK) return rc;
+  for (int b = 0; b < B; b++) {
+    HostLattice &L = items[idx[b]].L;
+    const int A = lens[b];
+    std::vector<double> total(A, 0.0);
+    for (int k = 0; k < A; k++)
+      for (int s = 0; s < 8; s++)
+        total[k] += std::expm1(std::max(0.f, y[((size_t)b * Lmax + k) * 8 + s]));
+    L.caps.assign(L.N, 0);
+    for (int v = 0; v < L.N; v++) {
+      if (L.layer[v] < 1) continue;
+      const int k = std::min(A - 1, (L.layer[v] - 1) / 3);
+      const double want = std::ceil(margin * total[k]) + 8.0;
+      L.caps[v] = (int32_t)std::min<double>(want, worst_room(L, v));
+    }
+  }
+  return SD_OK;
+}
+
+int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margin, int count,
+                const char *const *proteins, const double *codon_weights, int weights_shared,
+                const double *lambdas, sd_plan **out, int *item_status) {
+  sd_predictor *pred = const_cast<sd_predictor *>(cpred);
   if (!out) return SD_EINVAL;
   *out = nullptr;
   if (!energy || count < 0 || (count > 0 && (!proteins || !codon_weights || !lambdas)))
@@ -477,6 +556,15 @@ extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *co
     it.status = build_lattice(proteins[k], w, it.lambda, it.L);
     if (it.status == SD_OK && it.L.n > SD_MAX_NT) it.status = SD_EINVAL;
     if (it.status == SD_OK) it.status = range_check(energy, it.L);
+  }
+  if (pred) {
+    int rc = presize(pred, margin, p->items);
+    if (rc != SD_OK) {
+      delete p;
+      return rc;
+    }
+  }
+  for (auto &it : p->items) {
     if (it.status != SD_OK) continue;
     SdDesign d{};
     total += carve(nullptr, it.L, d);
@@ -535,6 +623,7 @@ extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *co
   *out = p;
   return SD_OK;
 }
+}  // namespace
 
 extern "C" int sd_plan_run(sd_plan *p, void *stream) {
   if (!p) return SD_EINVAL;
@@ -681,9 +770,86 @@ extern "C" int64_t sd_plan_device_bytes(const sd_plan *p) {
 
 extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
 
+// A presized candidate list that overflowed invalidates its design's run.
+// The regrow pass gives each such design worst-case room (a buffer of its
+// own, kept for later runs of the plan) and repeats the whole path for those
+// designs only, as one sub-batch in the plan's device order.
+namespace {
+int regrow_if_needed(sd_plan *p) {
+  std::vector<int> over;  // item indices, in device order
+  std::vector<std::pair<int, int>> by_dev;
+  for (size_t k = 0; k < p->items.size(); k++) {
+    PlanItem &it = p->items[k];
+    if (it.status != SD_OK || !it.d.cand_cap) continue;
+    int64_t flag = 0;
+    if (cudaMemcpy(&flag, it.d.tb + 3, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return SD_ECUDA;
+    if (flag) by_dev.push_back({it.dev_index, (int)k});
+  }
+  if (by_dev.empty()) return SD_OK;
+  std::sort(by_dev.begin(), by_dev.end());
+  for (auto &pr : by_dev) over.push_back(pr.second);
+  std::vector<SdDesign> sub;
+  std::vector<int> ns;
+  std::vector<int32_t> cpre(1, 0);
+  for (int k : over) {
+    PlanItem &it = p->items[k];
+    it.L.caps.clear();
+    const int N = it.L.N;
+    int64_t cap = 0;
+    std::vector<int64_t> off(N);
+    for (int v = 0; v < N; v++) {
+      off[v] = cap;
+      cap += worst_room(it.L, v);
+    }
+    const size_t off_bytes = ((size_t)N * 8 + 255) & ~(size_t)255;
+    const size_t b_bytes = ((size_t)std::max<int64_t>(cap, 1) * 8 + 255) & ~(size_t)255;
+    const size_t bytes = off_bytes + b_bytes + (size_t)std::max<int64_t>(cap, 1) * 4;
+    char *buf = nullptr;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) return SD_ENOMEM;
+    if (it.own_cand) cudaFree(it.own_cand);
+    it.own_cand = (int32_t *)buf;
+    SdDesign &d = it.d;
+    d.cand_off = (int64_t *)buf;
+    d.cand_B = (int64_t *)(buf + off_bytes);
+    d.cand_c = (int32_t *)(buf + off_bytes + b_bytes);
+    d.cand_cap = nullptr;
+    if (cudaMemcpy((void *)d.cand_off, off.data(), (size_t)N * 8, cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return SD_ECUDA;
+    p->hdesigns[it.dev_index] = d;
+    it.regrows++;
+    sub.push_back(d);
+    ns.push_back(it.L.n);
+    cpre.push_back(cpre.back() + it.L.n + 1);
+  }
+  if (cudaMemcpy(p->d_designs, p->hdesigns.data(), sizeof(SdDesign) * p->hdesigns.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return SD_ECUDA;
+  SdDesign *d_sub = nullptr;
+  int32_t *d_cpre = nullptr;
+  bool ok = cudaMalloc(&d_sub, sizeof(SdDesign) * sub.size()) == cudaSuccess &&
+            cudaMalloc(&d_cpre, sizeof(int32_t) * cpre.size()) == cudaSuccess &&
+            cudaMemcpy(d_sub, sub.data(), sizeof(SdDesign) * sub.size(), cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemcpy(d_cpre, cpre.data(), sizeof(int32_t) * cpre.size(),
+                       cudaMemcpyHostToDevice) == cudaSuccess;
+  int64_t nl = 0;
+  ok = ok && sd_k_run(d_sub, (int)sub.size(), ns.data(), d_cpre, p->energy->d, p->last_stream, &nl,
+                      nullptr, p->group) == 0;
+  ok = ok && cudaStreamSynchronize(p->last_stream) == cudaSuccess;
+  cudaFree(d_sub);
+  cudaFree(d_cpre);
+  return ok ? SD_OK : SD_ECUDA;
+}
+}  // namespace
+
 extern "C" int sd_plan_results(sd_plan *p, sd_result *outs, int *status) {
   if (!p || (!outs && !p->items.empty())) return SD_EINVAL;
   if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return SD_ECUDA;
+  {
+    int rc = regrow_if_needed(p);
+    if (rc != SD_OK) return rc;
+  }
   const int nd = (int)p->hdesigns.size();
   std::vector<int64_t> counts((size_t)nd * 4, 0);
   if (nd > 0) {
@@ -740,12 +906,37 @@ extern "C" int sd_plan_results(sd_plan *p, sd_result *outs, int *status) {
         r.retained_cells = c4[2];
         r.states = it.L.N;
         r.edges = it.L.E;
-        r.regrows = 0;
+        r.regrows = it.regrows;
       }
     }
     if (status) status[k] = st;
   }
   return SD_OK;
+}
+
+extern "C" int sd_plan_retention(const sd_plan *p, int item, int32_t *counts) {
+  if (!p || !counts || item < 0 || item >= (int)p->items.size()) return SD_EINVAL;
+  const PlanItem &it = p->items[item];
+  if (it.status != SD_OK) return it.status;
+  const int A = it.L.n / 3;
+  if (A == 0) return SD_OK;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return SD_ECUDA;
+  int32_t *d = nullptr;
+  if (cudaMalloc(&d, sizeof(int32_t) * 8 * A) != cudaSuccess) return SD_ENOMEM;
+  int rc = sd_k_retention(p->d_designs, it.dev_index, d, A, nullptr);
+  bool ok = rc == 0 && cudaMemcpy(counts, d, sizeof(int32_t) * 8 * A, cudaMemcpyDeviceToHost) ==
+                           cudaSuccess;
+  cudaFree(d);
+  return ok ? SD_OK : SD_ECUDA;
+}
+
+extern "C" int64_t sd_plan_candidate_room(const sd_plan *p) {
+  if (!p) return 0;
+  int64_t total = 0;
+  for (const auto &it : p->items)
+    if (it.status == SD_OK)
+      for (int v = 0; v < it.L.N; v++) total += room(it.L, v);
+  return total;
 }
 
 extern "C" int sd_plan_item_size(const sd_plan *p, int item, int32_t *n, int32_t *N, int32_t *E) {
@@ -825,6 +1016,7 @@ extern "C" int sd_plan_dump(const sd_plan *p, int item, int32_t *layer, int64_t 
         cudaMemcpy(off.data(), d.cand_off, N * 8, cudaMemcpyDeviceToHost) != cudaSuccess)
       return SD_ECUDA;
     for (int bb = 0; bb < N; bb++) {
+      cnt[bb] = std::min(cnt[bb], room(it.L, bb));  // a presized list that overflowed
       cc.resize(std::max(cnt[bb], 1));
       if (cnt[bb] > 0 && cudaMemcpy(cc.data(), d.cand_c + off[bb], (size_t)cnt[bb] * 4,
                                     cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -840,6 +1032,8 @@ extern "C" void sd_plan_free(sd_plan *p) {
   if (p->arena) cudaFree(p->arena);
   if (p->d_designs) cudaFree(p->d_designs);
   if (p->d_cpre) cudaFree(p->d_cpre);
+  for (auto &it : p->items)
+    if (it.own_cand) cudaFree(it.own_cand);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (int k = 0; k < 4; k++)

@@ -89,12 +89,15 @@ struct SdDesign {
   int64_t *W;
   int32_t *cand_cnt;      // N   |C_b|
   const int64_t *cand_off;// N   first entry of C_b
+  const int32_t *cand_cap;// N   entries reserved for C_b, or null when each list has its
+                          //     worst-case room; a list that outgrows a presized room sets
+                          //     tb[3] (the run is then repeated with worst-case room)
   int32_t *cand_c;        // start states of the retained candidates
   int64_t *cand_B;        // their scalar branch costs B(c,b)
   int64_t *Ext;           // N   exterior suffix values (Sec. 5 final-column exterior)
   uint32_t *Extk;         // N
   char *mrna, *structure; // n+1 each
-  int64_t *tb;            // traceback output: [0] energy, [1] path cost, [2] status
+  int64_t *tb;            // [0] energy, [1] path cost, [2] traceback status, [3] overflow
   int32_t *tb_stack;      // traceback work list, 4 ints per task
   int32_t tb_cap;         // tasks
   int32_t pad2;
@@ -124,6 +127,8 @@ int sd_internal_range_check(const struct sd_energy *E, int n, double qmax_sum);
 const SdParams *sd_internal_device_params(const struct sd_energy *E);
 int32_t sd_internal_hairpin_len(const struct sd_energy *E, int L);
 int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
+int sd_k_retention(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
+                   void *stream);
 #ifdef __cplusplus
 }
 #endif

@@ -932,7 +932,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
           upd(s2, s2k, v + e.cost + mlb, (uint32_t)k);
           TERM(2);
         }
-      const int cnt = D.cand_cnt[b];
+      const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
       for (int k = sub; k < cnt; k += G) {
         const int c = D.cand_c[off + k];
@@ -985,11 +985,16 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
       const int b = b0 + sb;
       int cnt = D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
+      const int cap = D.cand_cap ? __ldg(&D.cand_cap[b]) : 0x7fffffff;
       for (int sa = wa - 1; sa >= 0; sa--) {
         const int s = sa * SD_W + sb;
         if (Bs[s] < PSs[s]) {
-          D.cand_c[off + cnt] = a0 + sa;
-          D.cand_B[off + cnt] = Bs[s];
+          if (cnt < cap) {
+            D.cand_c[off + cnt] = a0 + sa;
+            D.cand_B[off + cnt] = Bs[s];
+          } else {
+            D.tb[3] = 1;  // presized room exceeded: this run is repeated
+          }
           cnt++;
         }
       }
@@ -1450,6 +1455,26 @@ __global__ void k_clear_cand(const SdDesign *__restrict__ designs) {
   const SdDesign &D = designs[blockIdx.y];
   for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < D.N; v += gridDim.x * blockDim.x)
     D.cand_cnt[v] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) D.tb[3] = 0;
+}
+
+// Retained candidates of one design by (codon position of the right endpoint,
+// span band): band = floor(log2(span)) - 2 clamped to [0, 7], i.e. spans
+// 5-7, 8-15, ..., 256-511, >= 512.  hist: A * 8 counters, zeroed by the caller.
+__global__ void k_retention(const SdDesign *__restrict__ designs, int item, int32_t *hist) {
+  const SdDesign &D = designs[item];
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < D.N; b += gridDim.x * blockDim.x) {
+    const int lb = D.layer[b];
+    if (lb < 1) continue;
+    const int k = (lb - 1) / 3;
+    const int cnt = D.cand_cap ? min(D.cand_cnt[b], D.cand_cap[b]) : D.cand_cnt[b];
+    const int64_t off = D.cand_off[b];
+    for (int q = 0; q < cnt; q++) {
+      const int span = lb - D.layer[D.cand_c[off + q]];
+      const int band = min(7, max(0, 31 - __clz(span) - 2));
+      atomicAdd(&hist[k * 8 + band], 1);
+    }
+  }
 }
 
 // per design: [0] Z, [1] finite direct intervals, [2] retained cell updates
@@ -1514,6 +1539,17 @@ int launch_fill(int G, const SdDesign *d_designs, int count, const int *ns, cons
 }
 
 }  // namespace
+
+extern "C" int sd_k_retention(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
+                              void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * 8 * (ncodons > 0 ? ncodons : 1), st) !=
+      cudaSuccess)
+    return -1;
+  k_retention<<<64, 256, 0, st>>>(d_designs, item, d_hist);
+  if (cudaGetLastError() != cudaSuccess) return -1;
+  return cudaStreamSynchronize(st) == cudaSuccess ? 0 : -1;
+}
 
 extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
