@@ -123,36 +123,59 @@ def predict_totals(pred: Predictor, items, idx):
     return [np.expm1(np.maximum(y[b, :ln[b]], 0.0)).sum(axis=1) for b in range(len(idx))]
 
 
+def load(path: str = DEFAULT_WEIGHTS) -> Predictor:
+    """A predictor with trained parameters (the shipped ones by default)."""
+    pred = Predictor()
+    pred.set_params(np.load(path))
+    return pred
+
+
 def evaluate(energy: Energy, pred: Predictor, items, margin: float = 2.0,
              max_nt_sq: float = 1.5e8):
-    """Run every item with worst-case room and with predicted room; return
-    the room totals, the regrow count and whether every design is identical."""
-    room_worst = room_pred = regrows = 0
+    """Run every item with worst-case room (the plain schedule) and with
+    predicted room; return the reserved room, the retained candidates, the
+    regrow count, the device bytes and wall times of both, and whether every
+    design is identical."""
+    room_worst = room_pred = regrows = retained = 0
+    bytes_worst = bytes_pred = 0
+    t_plain = t_pred = 0.0
     identical = True
     for grp in _chunks(items, max_nt_sq):
         sub = [items[k] for k in grp]
         args = ([p for p, _, _ in sub], np.stack([w for _, w, _ in sub]),
                 [lam for _, _, lam in sub])
+        t0 = time.perf_counter()
         plain = Plan(energy, *args)
-        pres = Plan(energy, *args, predictor=pred, margin=margin)
         try:
-            room_worst += plain.candidate_room
-            room_pred += pres.candidate_room
             plain.run()
-            pres.run()
-            r0, r1 = plain.results(), pres.results()
-            for a, b in zip(r0, r1):
-                regrows += b["regrows"]
-                for key in ("status", "mrna", "structure", "energy", "objective_fx", "Z",
-                            "retained_cells"):
-                    if a[key] != b[key]:
-                        identical = False
+            r0 = plain.results()
+            t_plain += time.perf_counter() - t0
+            room_worst += plain.candidate_room
+            bytes_worst += plain.device_bytes
         finally:
             plain.free()
+        t0 = time.perf_counter()
+        pres = Plan(energy, *args, predictor=pred, margin=margin)
+        try:
+            pres.run()
+            r1 = pres.results()
+            t_pred += time.perf_counter() - t0
+            room_pred += pres.candidate_room
+            bytes_pred += pres.device_bytes
+        finally:
             pres.free()
-    return {"room_worst": room_worst, "room_pred": room_pred, "regrows": regrows,
-            "designs": len(items), "identical": identical,
-            "room_ratio": room_pred / max(1, room_worst)}
+        for a, b in zip(r0, r1):
+            regrows += b["regrows"]
+            retained += a["Z"]
+            for key in ("status", "mrna", "structure", "energy", "objective_fx", "Z",
+                        "retained_cells"):
+                if a[key] != b[key]:
+                    identical = False
+    return {"room_worst": room_worst, "room_pred": room_pred, "retained": retained,
+            "regrows": regrows, "designs": len(items), "identical": identical,
+            "room_ratio": room_pred / max(1, room_worst),
+            "device_bytes_worst": bytes_worst, "device_bytes_pred": bytes_pred,
+            "wall_s_plain": t_plain, "wall_s_pred": t_pred}
 
 
 def main():

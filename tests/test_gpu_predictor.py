@@ -205,3 +205,16 @@ def test_trained_predictor_cuts_room(sd, E1):
     # what the trained network gains over worst-case room, at a bounded regrow rate
     assert ev["room_ratio"] < 0.6, ev
     assert ev["regrows"] <= ev["designs"] // 4, ev
+
+
+def test_shipped_predictor_on_unseen_proteins(sd, E1):
+    """The trained parameters shipped with the package, on proteins drawn
+    with a seed the training corpus did not use."""
+    from paper_2609_32308_b300 import retention
+    pred = retention.load()
+    items = retention.corpus(24, seed=999, hi=400)
+    ev = retention.evaluate(E1, pred, items, margin=2.0)
+    assert ev["identical"]
+    assert ev["regrows"] <= 2, ev
+    assert ev["room_ratio"] < 0.5, ev
+    assert ev["room_pred"] >= ev["retained"]
