@@ -155,11 +155,11 @@ int sd_plan_phase_times(const sd_plan *plan, float *ms3);
  * does, but without the exterior pass and the traceback. */
 int sd_plan_count_ops(sd_plan *plan, int64_t *ops);
 
-/* Threads cooperating on one layer pair in the fill: 1, 8 or 32 (default 32).
- * Results do not depend on it; speed does (1 suits large batches, 32 a single
- * design).  sd_plan_autotune runs the plan once per candidate (synchronously,
- * legacy default stream), keeps the fastest and writes the three fill times
- * (ms, in the order 1, 8, 32) to ms3 (may be NULL). */
+/* Threads cooperating on one layer pair in the fill: 8, 16 or 32 (default
+ * 32); anything else is SD_EINVAL.  Results do not depend on it; speed does.
+ * sd_plan_autotune runs the plan once per candidate (synchronously, legacy
+ * default stream), keeps the fastest and writes the three fill times (ms, in
+ * the order 8, 16, 32) to ms3 (may be NULL). */
 int sd_plan_set_group(sd_plan *plan, int group);
 int sd_plan_get_group(const sd_plan *plan);
 int sd_plan_autotune(sd_plan *plan, float *ms3);

@@ -275,7 +275,7 @@ class Plan:
         rc = lib().sd_plan_autotune(self.handle, _ptr(ms))
         if rc != SD_OK:
             raise SdError(rc, "sd_plan_autotune")
-        return dict(zip((1, 8, 32), (float(x) for x in ms)))
+        return dict(zip((8, 16, 32), (float(x) for x in ms)))
 
     def count_ops(self):
         """Algorithmic INT32 slots of the fill, per item (counting variant)."""

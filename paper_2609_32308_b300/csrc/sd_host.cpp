@@ -402,6 +402,10 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.in_mask = c.take<uint8_t>(N);
   d.out_mask = c.take<uint8_t>(N);
   d.hp_len = c.take<int32_t>(n + 1);
+  d.fo = c.take<SdFlatEdge>(std::max(L.E, 1));
+  d.fo_off = c.take<int32_t>(N + 1);
+  d.fi = c.take<SdFlatEdge>(std::max(L.E, 1));
+  d.fi_off = c.take<int32_t>(N + 1);
   const size_t ring = (size_t)SD_RING * (n + 1) * SD_SLOTS;
   d.H = c.take<int64_t>(ncell * SD_SLOTS);
   d.Hk = c.take<uint8_t>(ncell * SD_SLOTS);
@@ -449,6 +453,10 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
   }
   std::vector<int32_t> rooms(N);
   for (int v = 0; v < N; v++) rooms[v] = room(L, v);
+  std::vector<SdFlatEdge> fo(std::max(L.E, 1)), fi(std::max(L.E, 1));
+  std::vector<int32_t> fo_off(N + 1), fi_off(N + 1);
+  sd_internal_flatten((int)N, L.out.data(), L.out_cnt.data(), L.in.data(), L.in_cnt.data(),
+                      fo.data(), fo_off.data(), fi.data(), fi_off.data());
   auto cp = [](const void *dst, const void *src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice) ==
                              cudaSuccess;
@@ -459,7 +467,10 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
             cp(d.in, L.in.data(), L.in.size() * sizeof(SdEdge)) && cp(d.in_cnt, L.in_cnt.data(), N) &&
             cp(d.in_mask, L.in_mask.data(), N) && cp(d.out_mask, L.out_mask.data(), N) &&
             cp(d.hp_len, hp.data(), (n + 1) * 4) && cp(d.cand_off, off.data(), N * 8) &&
-            (!d.cand_cap || cp(d.cand_cap, rooms.data(), N * 4));
+            (!d.cand_cap || cp(d.cand_cap, rooms.data(), N * 4)) &&
+            cp(d.fo, fo.data(), (size_t)L.E * sizeof(SdFlatEdge)) &&
+            cp(d.fi, fi.data(), (size_t)L.E * sizeof(SdFlatEdge)) &&
+            cp(d.fo_off, fo_off.data(), (N + 1) * 4) && cp(d.fi_off, fi_off.data(), (N + 1) * 4);
   return ok ? SD_OK : SD_ECUDA;
 }
 
@@ -705,7 +716,7 @@ extern "C" int sd_plan_set_timing(sd_plan *p, int enable);
 extern "C" int sd_plan_phase_times(const sd_plan *p, float *ms);
 
 extern "C" int sd_plan_set_group(sd_plan *p, int group) {
-  if (!p || !(group == 1 || group == 8 || group == 32)) return SD_EINVAL;
+  if (!p || !(group == 8 || group == 16 || group == 32)) return SD_EINVAL;
   if (group != p->group && p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
@@ -720,7 +731,7 @@ extern "C" int sd_plan_get_group(const sd_plan *p) { return p ? p->group : SD_EI
 // events on the legacy default stream) and keep the fastest.
 extern "C" int sd_plan_autotune(sd_plan *p, float *ms_out) {
   if (!p) return SD_EINVAL;
-  static const int cand[3] = {1, 8, 32};
+  static const int cand[3] = {8, 16, 32};
   if (p->hdesigns.empty()) return SD_OK;
   const bool had = p->timing;
   int rc = sd_plan_set_timing(p, 1);
@@ -1092,6 +1103,25 @@ extern "C" const char *sd_strerror(int code) {
 // internal helpers shared with the fixed-scratch entry point (sd_noalloc.cu)
 // ---------------------------------------------------------------------------
 extern "C" char sd_internal_translate(int x, int y, int z) { return translate(x, y, z); }
+extern "C" void sd_internal_flatten(int N, const SdEdge *out, const uint8_t *out_cnt,
+                                    const SdEdge *in, const uint8_t *in_cnt, SdFlatEdge *fo,
+                                    int32_t *fo_off, SdFlatEdge *fi, int32_t *fi_off) {
+  int32_t eo = 0, ei = 0;
+  for (int v = 0; v < N; v++) {
+    fo_off[v] = eo;
+    for (int k = 0; k < out_cnt[v]; k++) {
+      const SdEdge &e = out[(size_t)v * SD_MAXOUT + k];
+      fo[eo++] = SdFlatEdge{v, e.other * 4 + e.label, e.cost};
+    }
+    fi_off[v] = ei;
+    for (int k = 0; k < in_cnt[v]; k++) {
+      const SdEdge &e = in[(size_t)v * SD_MAXIN + k];
+      fi[ei++] = SdFlatEdge{v, e.other * 4 + e.label, e.cost};
+    }
+  }
+  fo_off[N] = eo;
+  fi_off[N] = ei;
+}
 extern "C" int64_t sd_internal_codon_fx(double lambda, double w) { return codon_fx(lambda, w); }
 extern "C" int sd_internal_range_check(const sd_energy *E, int n, double qmax_sum) {
   HostLattice L;

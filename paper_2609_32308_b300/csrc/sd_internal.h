@@ -37,6 +37,16 @@ struct SdEdge {
   int64_t cost;    // fixed-point codon cost (non-zero only on 3rd codon edges)
 };
 
+// An edge in a flat list: the out-edges of all states by (source, label), or
+// the in-edges by (target, label, source).  States are numbered layer by
+// layer, so the edges leaving (entering) the states of layers l0..l1 form one
+// contiguous range of the list.
+struct SdFlatEdge {
+  int32_t v;       // the state whose list holds the edge (source, resp. target)
+  int32_t wl;      // the other end * 4 + label
+  int64_t cost;
+};
+
 // Nearest-neighbour parameters on the device (integer dcal/mol).
 struct SdParams {
   int32_t stack[6][6];
@@ -66,6 +76,10 @@ struct SdDesign {
   const uint8_t *in_mask; // N, bit l set iff some edge with label l enters the state
   const uint8_t *out_mask;// N, bit l set iff the state has an out-edge with label l
   const int32_t *hp_len;  // hairpin length energy for L = 0..n (lxc extrapolation > 30)
+  const SdFlatEdge *fo;   // E out-edges by (source, label)
+  const int32_t *fo_off;  // N+1: out-edges of state v are fo[fo_off[v] .. fo_off[v+1])
+  const SdFlatEdge *fi;   // E in-edges by (target, label, source)
+  const int32_t *fi_off;  // N+1
   // Every value comes with the canonical key of the option attaining it (the
   // lexicographically smallest (value, key)); the traceback follows keys.
   int64_t *H;             // ncell*SLOTS  min path cost between states
@@ -112,7 +126,7 @@ extern "C" {
 // d_cpre[d] = sum over d' < d of (ns[d'] + 1), count + 1 entries on the device.
 // events: NULL or four cudaEvent_t recorded before the fill, after the fill,
 // after the exterior pass and after the traceback, on `stream`.
-// group: threads per layer pair in the fill (1, 8 or 32).
+// group: threads per layer pair in the fill (8, 16 or 32).
 int sd_k_run(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
              const SdParams *d_params, void *stream, int64_t *launches, void *const *events,
              int group);
@@ -126,6 +140,11 @@ int64_t sd_internal_codon_fx(double lambda, double w);
 int sd_internal_range_check(const struct sd_energy *E, int n, double qmax_sum);
 const SdParams *sd_internal_device_params(const struct sd_energy *E);
 int32_t sd_internal_hairpin_len(const struct sd_energy *E, int L);
+// flat edge lists (fo, fi: E entries each; fo_off, fi_off: N+1) from the
+// per-state lists
+void sd_internal_flatten(int N, const SdEdge *out, const uint8_t *out_cnt, const SdEdge *in,
+                         const uint8_t *in_cnt, SdFlatEdge *fo, int32_t *fo_off, SdFlatEdge *fi,
+                         int32_t *fi_off);
 int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
 int sd_k_retention(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
                    void *stream);

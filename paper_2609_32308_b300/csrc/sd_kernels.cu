@@ -1,10 +1,12 @@
 // sd_kernels.cu -- sm_103a kernels of the exact codon-lattice design DP.
 //
 // Span wavefront (Algorithm 1, Sec. 5).  One launch per span g processes every
-// layer pair (i, i+g) of every design in the batch (grid.y = design), one warp
-// per layer pair.  The paper separates closed/gap values, multiloop values and
-// exterior values by barriers; here all phases of one layer pair run in the
-// warp that owns it, because each only reads smaller spans or the same cell:
+// layer pair (i, i+g) of every design in the batch (a work queue over
+// (design, layer pair), longest design first), one group of 8, 16 or 32
+// threads per layer pair.  The paper separates closed/gap values, multiloop
+// values and exterior values by barriers; here all phases of one layer pair run
+// in the group that owns it, because each only reads smaller spans or the same
+// cell:
 //   H      min path cost a->b (gap cells)                       span g-1
 //   Ihat   inner pair + its loop-side mismatch (two-loop inner)  span g-2
 //   IL     generic internal loops below an outer pair            spans g-2..g-26
@@ -216,7 +218,13 @@ struct Fv {
   const int64_t *H;
   const uint8_t *Hk;
   const int64_t *V;
+  const int32_t *__restrict__ lay;
+  const SdFlatEdge *__restrict__ fo;
+  const int32_t *__restrict__ fo_off;
+  const SdFlatEdge *__restrict__ fi;
+  const int32_t *__restrict__ fi_off;
   __device__ __forceinline__ int ls(int l) const { return __ldg(lst + l); }
+  __device__ __forceinline__ int layer(int v) const { return __ldg(lay + v); }
   __device__ __forceinline__ int w(int l) const { return __ldg(lst + l + 1) - __ldg(lst + l); }
   __device__ __forceinline__ int doff(int s) const { return (s - 1) * (n + 1) - (((s - 1) * s) >> 1); }
   // packed slot of (layer lx, slot sx) -> (layer ly, slot sy), ly > lx
@@ -247,6 +255,16 @@ struct Fv {
   }
 };
 
+// Gap values of the two ends of a layer pair, staged in shared memory per
+// group: hl[l][c*2 + s] = H(slot s of layer i -> slot c of layer i+l),
+// hr[l][c*2 + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW,
+// with the (first, last) label keys; the two-loop options read them many times.
+constexpr int SD_GAPW = SD_MAXTWO + 1;
+struct GapStage {
+  int64_t hl[SD_GAPW][4], hr[SD_GAPW][4];
+  uint8_t hlk[SD_GAPW][4], hrk[SD_GAPW][4];
+};
+
 // lexicographic minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
 __device__ __forceinline__ void best_inner(const int64_t (&vv)[6], const int32_t (*tab)[16], int idx,
                                            int64_t &bv, int &bt) {
@@ -263,47 +281,70 @@ __device__ __forceinline__ void best_inner(const int64_t (&vv)[6], const int32_t
     }
 }
 
-// one outer type t per call: the running (value, key) minimum of Q_t
-#define FOR_T(body) \
-  do {              \
-    body;           \
-  } while (0)
+// lexicographic minimum over the inner pair types of vv[ti] + AU(rev ti)
+__device__ __forceinline__ void best_au(const int64_t (&vv)[6], const int32_t *au, int64_t &bv,
+                                        int &bt) {
+  bv = SD_INF;
+  bt = 7;
+#pragma unroll
+  for (int ti = 0; ti < 6; ti++)
+    if (fin(vv[ti])) {
+      const int64_t v = vv[ti] + fx(au[c_rev[ti]]);
+      if (v < bv) {
+        bv = v;
+        bt = ti;
+      }
+    }
+}
+
+// All outer pair types of one closed-interior cell at once: (qv[t], qk[t]) is
+// the running (value, key) minimum of Q_t for every t in the type mask tm
+// (the same for every thread of a group).  tab(t) is the outer-type part of
+// the loop energy; the rest of the term is shared by the types.
+template <bool COUNT, class Tab>
+__device__ __forceinline__ void upd6(int64_t (&qv)[6], uint32_t (&qk)[6], int tm, int64_t base,
+                                     uint32_t key, int nadd, unsigned long long &ops,
+                                     const Tab &tab) {
+#pragma unroll
+  for (int t = 0; t < 6; t++)
+    if ((tm >> t) & 1) {
+      upd(qv[t], qk[t], base + fx(tab(t)), key);
+      if (COUNT) ops += 2 * (nadd + 1);
+    }
+}
 
 // ---------------------------------------------------------------------------
-// closed-interior value Q_t(x, y) for one outer type t: the loop
-// closed by an outer pair of type t whose interior path runs from x (after
-// the 5' nucleotide of the pair) to y (before its 3' nucleotide).  x is slot
-// sx of layer lx, y slot sy of layer ly.  The work items of one layer pair are
-// spread over its G threads:
-//   it 0        hairpin
-//   it 1..31    l1 = 0, l2 = it-1        (stack, right bulges)
-//   it 32..61   l2 = 0, l1 = it-31       (left bulges)
-//   it 62..90   l1 = 1, l2 = it-61       (1x1, 1x2, 1xn)
-//   it 91..118  l2 = 1, l1 = it-89       (2x1, nx1)
-//   it 119..121 2x2, 2x3, 3x2
-//   it 122      generic internal loops through IL
-//   it 123      multiloop
+// closed-interior values Q_t(x, y), every outer type t of the mask tm: the
+// loop closed by an outer pair of type t whose interior path runs from x
+// (after the 5' nucleotide of the pair) to y (before its 3' nucleotide); x is
+// slot sx of layer lx, y slot sy of layer ly.  The options are split into
+// classes, and inside a class the G threads of the group take consecutive
+// entries of one flat list, so that every thread runs the same inner loops
+// (over the out-edges of x and the in-edges of y, the same for the group):
+//   hairpin        out-edges of x x in-edges of y (explicit paths for L = 3, 4, 6)
+//   stack, bulges  the states of the inner pair's moving end (l1 = 0 or l2 = 0)
+//   1 x n          out-edges of the states d of the inner pair (l1 = 1)
+//   n x 1          in-edges of the states c of the inner pair (l2 = 1, l1 >= 2)
+//   2x2, 2x3, 3x2  (in-edge of c, out-edge of d) pairs
+//   generic        out-edges of x x in-edges of y, through the IL table
+//   multiloop      one term
 // Where the loop energy splits into a part that depends on the inner pair and
 // a part that depends on the outer one, the best inner type comes from the
-// inner cell's precomputed table.
+// inner cell's precomputed table W.
 // ---------------------------------------------------------------------------
-// Item classes {first item, count, lane rotation}: the two heavy classes
-// (1xn and nx1) go first on lanes 0.., bulges fill in, the small classes take
-// the lanes the heavy ones leave free, so lanes of a group carry similar work.
-constexpr int Q_CLASSES = 8;
-__constant__ int c_qclass[Q_CLASSES][3] = {{62, 29, 0}, {91, 28, 0}, {1, 31, 1},   {32, 30, 2},
-                                           {119, 3, 29}, {0, 1, 31}, {122, 1, 30}, {123, 1, 29}};
-
-template <bool COUNT>
-__device__ __forceinline__ void q_item(const Fv &F, const SdDesign &D, const SdParams &P,
-                                       const SmallTables &T, int it, int x, int y, int lx, int sx,
-                                       int ly, int sy, int t, int64_t &qv, uint32_t &qk,
-                                       unsigned long long &ops) {
+template <int G, bool COUNT>
+__device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdParams &P,
+                                       const SmallTables &T, int sub, int x, int y, int lx,
+                                       int sx, int ly, int sy, int tm, int64_t (&qv)[6],
+                                       uint32_t (&qk)[6], unsigned long long &ops,
+                                       const GapStage &GS) {
   const int g = ly - lx;
-  if (it == 0) {
-    if (g < 3) return;
-    if (g == 3 || g == 4 || g == 6) {
-      // every interior path, lexicographic label order
+  const int nox = F.nout(x), niy = F.nin(y);
+  const int lx1s = F.ls(lx + 1), ly1s = F.ls(ly - 1);
+  // ---- hairpin (loop length L = g) ----
+  if (g == 3 || g == 4 || g == 6) {
+    if (sub == 0) {
+      // every interior path, lexicographic label order; special loops by sequence
       int st[8], kk[8];
       int64_t cst[8];
       uint32_t labs[8];
@@ -315,10 +356,12 @@ __device__ __forceinline__ void q_item(const Fv &F, const SdDesign &D, const SdP
       while (depth >= 0) {
         if (depth == g) {
           const uint32_t lb = labs[g];
-          FOR_T({
-            upd(qv, qk, fx(hairpin_seq_e(P, D.hp_len, t, lb, g)) + cst[g], lb);
-            TERM(g);
-          });
+#pragma unroll
+          for (int t = 0; t < 6; t++)
+            if ((tm >> t) & 1) {
+              upd(qv[t], qk[t], fx(hairpin_seq_e(P, D.hp_len, t, lb, g)) + cst[g], lb);
+              TERM(g);
+            }
           depth--;
           continue;
         }
@@ -337,347 +380,287 @@ __device__ __forceinline__ void q_item(const Fv &F, const SdDesign &D, const SdP
         kk[depth + 1] = 0;
         depth++;
       }
-    } else {
-      const int l1s = F.ls(lx + 1), l2s = F.ls(ly - 1);
-      const int64_t he = fx(__ldg(&D.hp_len[g]));
-      for (int a = 0; a < F.nout(x); a++) {
-        const SdEdge e1 = F.out(x, a);
-        for (int b = 0; b < F.nin(y); b++) {
-          const SdEdge e2 = F.in(y, b);
-          const int64_t h = F.Hh(lx + 1, e1.other - l1s, ly - 1, e2.other - l2s);
-          if (!fin(h)) continue;
-          const int64_t base = e1.cost + e2.cost + h + he;
-          const uint32_t key = (uint32_t)(e1.label * 4 + e2.label);
-          FOR_T({
-            upd(qv, qk, base + fx(T.mmH[t][e1.label * 4 + e2.label]), key);
-            TERM(3);
-          });
-        }
-      }
     }
-    return;
+  } else if (g >= 5) {
+    const int64_t he = fx(__ldg(&D.hp_len[g]));
+    for (int k = sub; k < nox * niy; k += G) {
+      const int a = k / niy, b = k - a * niy;
+      const SdEdge e1 = F.out(x, a), e2 = F.in(y, b);
+      const int64_t h = F.Hh(lx + 1, e1.other - lx1s, ly - 1, e2.other - ly1s);
+      if (!fin(h)) continue;
+      const int idx = e1.label * 4 + e2.label;
+      upd6<COUNT>(qv, qk, tm, e1.cost + e2.cost + h + he, (uint32_t)idx, 3, ops,
+                  [&](int t) { return T.mmH[t][idx]; });
+    }
   }
-  if (it <= 61) {  // stack and bulges: one side empty
-    const bool right = it <= 31;
-    const int l = right ? it - 1 : it - 31;
-    if (g - l < 5) return;
-    const int lo = right ? ly - l : lx + l;  // layer of the inner state that moves
-    const int wo = F.w(lo);
-    for (int so = 0; so < wo; so++) {
+  if (g < 5) return;
+  // ---- stack and bulges: right side (l1 = 0, l2 = l >= 0), left side (l2 = 0, l1 = l >= 1) ----
+  {
+    const int rlo = max(ly - SD_MAXTWO, lx + 5);  // layers of d on the right side
+    const int r0 = F.ls(rlo), nr = F.ls(ly + 1) - r0;
+    const int lhi = min(lx + SD_MAXTWO, ly - 5);  // layers of c on the left side
+    const int c0 = lx1s, nl = lhi >= lx + 1 ? F.ls(lhi + 1) - c0 : 0;
+    for (int k = sub; k < nr + nl; k += G) {
+      const bool right = k < nr;
+      const int v = right ? r0 + k : c0 + (k - nr);
+      const int lv = F.layer(v), sv = v - F.ls(lv);
+      const int l = right ? ly - lv : lv - lx;
       int64_t h = 0;
       int hk = 0;
       if (l > 0) {
-        const int q = right ? F.cs(lo, so, ly, sy) : F.cs(lx, sx, lo, so);
-        h = F.H[q];
+        h = right ? GS.hr[l][sv * 2 + sy] : GS.hl[l][sv * 2 + sx];
         if (!fin(h)) continue;
-        hk = F.Hk[q];
-      } else if (so != sy) {
+        hk = right ? GS.hrk[l][sv * 2 + sy] : GS.hlk[l][sv * 2 + sx];
+      } else if (sv != sy) {
         continue;
       }
-      const int cs = right ? sx : so, ds = right ? so : sy;
+      const int cs = right ? sx : sv, ds = right ? sv : sy;
       const uint32_t kb = right ? tl_key(0, l, cs, ds, 0, 0, 0, hk >> 2, hk & 3)
                                 : tl_key(l, 0, cs, ds, 0, hk >> 2, hk & 3, 0, 0);
       if (l >= 2) {
         // bulge: bulge[l] + AU(t) + AU(inner); best inner type from the inner table
-        const int rc = right ? F.rs(lx, sx, lo, so) : F.rs(lo, so, ly, sy);
+        const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
         const int64_t pk = D.W[(int64_t)rc * SD_WN + 48];
         if (!fin(pk)) continue;
-        const int64_t b2 = (pk >> 3) + h + fx(T.bulge[l]);
-        const uint32_t key = kb | ((uint32_t)(pk & 7) << 8);
-        FOR_T({
-          upd(qv, qk, b2 + fx(T.au[t]), key);
-          TERM(2);
-        });
+        upd6<COUNT>(qv, qk, tm, (pk >> 3) + h + fx(T.bulge[l]), kb | ((uint32_t)(pk & 7) << 8), 2,
+                    ops, [&](int t) { return T.au[t]; });
       } else {
         int64_t vv[6];
-        F.v6(right ? F.cs(lx, sx, lo, so) : F.cs(lo, so, ly, sy), vv);
+        F.v6(right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy), vv);
         const int64_t e1 = h + fx(l == 1 ? T.bulge[1] : 0);
 #pragma unroll
         for (int ti = 0; ti < 6; ti++) {
           if (!fin(vv[ti])) continue;
           const int s = c_rev[ti];
-          const uint32_t key = kb | ((uint32_t)ti << 8);
-          FOR_T({
-            upd(qv, qk, vv[ti] + e1 + fx(T.stack[t][s]), key);
-            TERM(2);
-          });
+          upd6<COUNT>(qv, qk, tm, vv[ti] + e1, kb | ((uint32_t)ti << 8), 2, ops,
+                      [&](int t) { return T.stack[t][s]; });
         }
       }
     }
-    return;
   }
-  if (it <= 90) {  // l1 = 1: 1x1, 1x2, 1xn
-    const int l2 = it - 61;
-    if (g - 1 - l2 < 5) return;
-    const int ld = ly - l2, wd = F.w(ld), lds = F.ls(ld);
-    const int lc = lx + 1, lcs = F.ls(lc);
-    const int ld1s = F.ls(ld + 1), ly1s = F.ls(ly - 1);
-    const int64_t e0 = fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
-    for (int a = 0; a < F.nout(x); a++) {
-      const SdEdge ec = F.out(x, a);
-      const int p = ec.label, cs = ec.other - lcs;
-      for (int ds = 0; ds < wd; ds++) {
-        const int d = lds + ds;
-        int64_t vv[6];
-        if (l2 <= 2) {
-          F.v6(F.cs(lc, cs, ld, ds), vv);
-          if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
-            continue;
+  // ---- 1 x n: l1 = 1 (nucleotide p after the outer 5' end), l2 >= 1; entries are
+  // the out-edges r1 of the inner pair's 3' end d ----
+  {
+    const int lc = lx + 1;
+    const int dlo = max(lx + 6, ly - (SD_MAXTWO - 1)), dhi = ly - 1;
+    const int k0 = dlo <= dhi ? F.fo_off[F.ls(dlo)] : 0;
+    const int k1 = dlo <= dhi ? F.fo_off[F.ls(dhi + 1)] : 0;
+    for (int k = k0 + sub; k < k1; k += G) {
+      const SdFlatEdge r1 = F.fo[k];
+      const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
+      const int ld = F.layer(d), ds = d - F.ls(ld), l2 = ly - ld;
+      if (l2 >= 3) {
+        const int lus = F.ls(ld + 1);
+        const int64_t e0 = fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
+        for (int a = 0; a < nox; a++) {
+          const SdEdge ec = F.out(x, a);
+          const int p = ec.label, cs = ec.other - lx1s;
+          const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR];
+          if (!fin(pk)) continue;
+          const int64_t base = (pk >> 3) + ec.cost + r1.cost + e0;
+          const int wt = (int)(pk & 7);
+          for (int b2 = 0; b2 < niy; b2++) {
+            const SdEdge r2 = F.in(y, b2);
+            const int64_t h = F.Hh(ld + 1, u - lus, ly - 1, r2.other - ly1s);
+            if (!fin(h)) continue;
+            const int lR = r2.label;
+            upd6<COUNT>(qv, qk, tm, base + h + r2.cost, tl_key(1, l2, cs, ds, wt, p, p, fR, lR), 5,
+                        ops, [&](int t) { return T.mm1n[t][p * 4 + lR]; });
+          }
         }
-        for (int b = 0; b < F.nout(d); b++) {
-          const SdEdge r1 = F.out(d, b);
-          const int fR = r1.label;
-          if (l2 >= 3) {
-            const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR];
-            if (!fin(pk)) continue;
-            const int64_t wv = pk >> 3;
-            const int wt = (int)(pk & 7);
-            const int64_t base = wv + ec.cost + r1.cost + e0;
-            for (int b2 = 0; b2 < F.nin(y); b2++) {
-              const SdEdge r2 = F.in(y, b2);
-              const int64_t h = F.Hh(ld + 1, r1.other - ld1s, ly - 1, r2.other - ly1s);
-              if (!fin(h)) continue;
-              const int lR = r2.label;
-              const uint32_t key = tl_key(1, l2, cs, ds, wt, p, p, fR, lR);
-              const int64_t b3 = base + h + r2.cost;
-              FOR_T({
-                upd(qv, qk, b3 + fx(T.mm1n[t][p * 4 + lR]), key);
-                TERM(5);
-              });
-            }
-          } else if (l2 == 1) {
-            if (r1.other != y) continue;
-            const int64_t base = ec.cost + r1.cost;
+      } else if (l2 == 1) {
+        if (u != y) continue;
+        for (int a = 0; a < nox; a++) {
+          const SdEdge ec = F.out(x, a);
+          const int p = ec.label, cs = ec.other - lx1s;
+          int64_t vv[6];
+          F.v6(F.cs(lc, cs, ld, ds), vv);
+          const int64_t base = ec.cost + r1.cost;
+#pragma unroll
+          for (int ti = 0; ti < 6; ti++) {
+            if (!fin(vv[ti])) continue;
+            const int s = c_rev[ti];
+            upd6<COUNT>(qv, qk, tm, vv[ti] + base, tl_key(1, 1, cs, ds, ti, p, p, fR, fR), 3, ops,
+                        [&](int t) { return P.int11[t][s][p * 4 + fR]; });
+          }
+        }
+      } else {  // l2 == 2: explicit 2-edge right side
+        for (int b2 = 0; b2 < F.nout(u); b2++) {
+          const SdEdge r2 = F.out(u, b2);
+          if (r2.other != y) continue;
+          const int lR = r2.label;
+          for (int a = 0; a < nox; a++) {
+            const SdEdge ec = F.out(x, a);
+            const int p = ec.label, cs = ec.other - lx1s;
+            int64_t vv[6];
+            F.v6(F.cs(lc, cs, ld, ds), vv);
+            const int64_t base = ec.cost + r1.cost + r2.cost;
 #pragma unroll
             for (int ti = 0; ti < 6; ti++) {
               if (!fin(vv[ti])) continue;
               const int s = c_rev[ti];
-              const uint32_t key = tl_key(1, 1, cs, ds, ti, p, p, fR, fR);
-              FOR_T({
-                upd(qv, qk, vv[ti] + base + fx(P.int11[t][s][p * 4 + fR]), key);
-                TERM(3);
-              });
-            }
-          } else {  // l2 == 2: explicit 2-edge right side
-            const int m = r1.other;
-            for (int b2 = 0; b2 < F.nout(m); b2++) {
-              const SdEdge r2 = F.out(m, b2);
-              if (r2.other != y) continue;
-              const int lR = r2.label;
-              const int64_t base = ec.cost + r1.cost + r2.cost;
-#pragma unroll
-              for (int ti = 0; ti < 6; ti++) {
-                if (!fin(vv[ti])) continue;
-                const int s = c_rev[ti];
-                const uint32_t key = tl_key(1, 2, cs, ds, ti, p, p, fR, lR);
-                FOR_T({
-                  upd(qv, qk, vv[ti] + base + fx(P.int21[t][s][p * 16 + fR * 4 + lR]), key);
-                  TERM(4);
-                });
-              }
+              upd6<COUNT>(qv, qk, tm, vv[ti] + base, tl_key(1, 2, cs, ds, ti, p, p, fR, lR), 4,
+                          ops, [&](int t) { return P.int21[t][s][p * 16 + fR * 4 + lR]; });
             }
           }
         }
       }
     }
-    (void)lds;
-    return;
   }
-  if (it <= 118) {  // l2 = 1, l1 >= 2: 2x1, nx1
-    const int l1 = it - 89;
-    if (g - 1 - l1 < 5) return;
-    const int lc = lx + l1, wc = F.w(lc), lcs = F.ls(lc);
-    const int ld = ly - 1, lds = F.ls(ld);
-    const int lx1s = F.ls(lx + 1), lc1s = F.ls(lc - 1);
-    const int64_t e0 = fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
-    for (int b = 0; b < F.nin(y); b++) {
-      const SdEdge er = F.in(y, b);
-      const int r = er.label, ds = er.other - lds;
-      for (int cs = 0; cs < wc; cs++) {
-        const int c = lcs + cs;
-        int64_t vv[6];
-        if (l1 == 2) {
+  // ---- n x 1: l2 = 1 (nucleotide r before the outer 3' end), l1 >= 2; entries are
+  // the in-edges p2 of the inner pair's 5' end c ----
+  {
+    const int ld = ly - 1;
+    const int clo = lx + 2, chi = min(lx + SD_MAXTWO - 1, ly - 6);
+    const int k0 = clo <= chi ? F.fi_off[F.ls(clo)] : 0;
+    const int k1 = clo <= chi ? F.fi_off[F.ls(chi + 1)] : 0;
+    for (int k = k0 + sub; k < k1; k += G) {
+      const SdFlatEdge p2 = F.fi[k];
+      const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
+      const int lc = F.layer(c), cs = c - F.ls(lc), l1 = lc - lx;
+      if (l1 >= 3) {
+        const int lws = F.ls(lc - 1);
+        const int64_t e0 = fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
+        for (int b = 0; b < niy; b++) {
+          const SdEdge er = F.in(y, b);
+          const int r = er.label, ds = er.other - ly1s;
+          const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r];
+          if (!fin(pk)) continue;
+          const int64_t base = (pk >> 3) + er.cost + p2.cost + e0;
+          const int wt = (int)(pk & 7);
+          for (int a = 0; a < nox; a++) {
+            const SdEdge p1 = F.out(x, a);
+            const int64_t h = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lws);
+            if (!fin(h)) continue;
+            const int fL = p1.label;
+            upd6<COUNT>(qv, qk, tm, base + h + p1.cost, tl_key(l1, 1, cs, ds, wt, fL, lL, r, r), 5,
+                        ops, [&](int t) { return T.mm1n[t][fL * 4 + r]; });
+          }
+        }
+      } else {  // l1 == 2: explicit 2-edge left side
+        for (int b = 0; b < niy; b++) {
+          const SdEdge er = F.in(y, b);
+          const int r = er.label, ds = er.other - ly1s;
+          int64_t vv[6];
           F.v6(F.cs(lc, cs, ld, ds), vv);
-          if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
-            continue;
-        }
-        for (int a2 = 0; a2 < F.nin(c); a2++) {
-          const SdEdge p2 = F.in(c, a2);
-          const int lL = p2.label;
-          if (l1 >= 3) {
-            const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r];
-            if (!fin(pk)) continue;
-            const int64_t wv = pk >> 3;
-            const int wt = (int)(pk & 7);
-            const int64_t base = wv + er.cost + p2.cost + e0;
-            for (int a = 0; a < F.nout(x); a++) {
-              const SdEdge p1 = F.out(x, a);
-              const int64_t h = F.Hh(lx + 1, p1.other - lx1s, lc - 1, p2.other - lc1s);
-              if (!fin(h)) continue;
-              const int fL = p1.label;
-              const uint32_t key = tl_key(l1, 1, cs, ds, wt, fL, lL, r, r);
-              const int64_t b3 = base + h + p1.cost;
-              FOR_T({
-                upd(qv, qk, b3 + fx(T.mm1n[t][fL * 4 + r]), key);
-                TERM(5);
-              });
-            }
-          } else {  // l1 == 2: explicit 2-edge left side
-            for (int a = 0; a < F.nout(x); a++) {
-              const SdEdge p1 = F.out(x, a);
-              if (p1.other != p2.other) continue;
-              const int fL = p1.label;
-              const int64_t base = er.cost + p1.cost + p2.cost;
+          for (int a = 0; a < nox; a++) {
+            const SdEdge p1 = F.out(x, a);
+            if (p1.other != w) continue;
+            const int fL = p1.label;
+            const int64_t base = er.cost + p1.cost + p2.cost;
 #pragma unroll
-              for (int ti = 0; ti < 6; ti++) {
-                if (!fin(vv[ti])) continue;
-                const int s = c_rev[ti];
-                const uint32_t key = tl_key(2, 1, cs, ds, ti, fL, lL, r, r);
-                FOR_T({
-                  upd(qv, qk, vv[ti] + base + fx(P.int21[s][t][r * 16 + fL * 4 + lL]), key);
-                  TERM(4);
-                });
-              }
+            for (int ti = 0; ti < 6; ti++) {
+              if (!fin(vv[ti])) continue;
+              const int s = c_rev[ti];
+              upd6<COUNT>(qv, qk, tm, vv[ti] + base, tl_key(2, 1, cs, ds, ti, fL, lL, r, r), 4,
+                          ops, [&](int t) { return P.int21[s][t][r * 16 + fL * 4 + lL]; });
             }
           }
         }
       }
     }
-    return;
   }
-  if (it <= 121) {  // 2x2, 2x3, 3x2
-    const int cls = it - 119;
+  // ---- 2x2, 2x3, 3x2: entries are (in-edge p2 of c, out-edge r1 of d) ----
+#pragma unroll 1
+  for (int cls = 0; cls < 3; cls++) {
     const int l1 = cls == 2 ? 3 : 2, l2 = cls == 1 ? 3 : 2;
-    if (g - l1 - l2 < 5) return;
+    if (g - l1 - l2 < 5) continue;
     const int lc = lx + l1, ld = ly - l2;
-    const int wc = F.w(lc), wd = F.w(ld), lcs = F.ls(lc), lds = F.ls(ld);
-    const int lx1s = F.ls(lx + 1), lc1s = F.ls(lc - 1), ld1s = F.ls(ld + 1), ly1s = F.ls(ly - 1);
-    for (int cs = 0; cs < wc; cs++)
-      for (int ds = 0; ds < wd; ds++) {
-        const int c = lcs + cs, d = lds + ds;
-        int64_t vv[6];
-        if (cls == 0) {
-          F.v6(F.cs(lc, cs, ld, ds), vv);
-          if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
-            continue;
-        }
-        for (int a2 = 0; a2 < F.nin(c); a2++) {
-          const SdEdge p2 = F.in(c, a2);
-          for (int b = 0; b < F.nout(d); b++) {
-            const SdEdge r1 = F.out(d, b);
-            // inner part: best inner type for this (lL, fR) (2x3 / 3x2 only)
-            int64_t wv = SD_INF;
-            int wt = 7;
-            if (cls) {
-              const int64_t pk =
-                  D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + p2.label * 4 + r1.label];
-              if (fin(pk)) {
-                wv = pk >> 3;
-                wt = (int)(pk & 7);
-              }
-            }
-            if (cls && !fin(wv)) continue;
-            for (int a = 0; a < F.nout(x); a++) {
-              const SdEdge p1 = F.out(x, a);
-              const int64_t hl = F.Hh(lx + 1, p1.other - lx1s, lc - 1, p2.other - lc1s);
-              if (!fin(hl)) continue;
-              for (int b2 = 0; b2 < F.nin(y); b2++) {
-                const SdEdge r2 = F.in(y, b2);
-                const int64_t hr = F.Hh(ld + 1, r1.other - ld1s, ly - 1, r2.other - ly1s);
-                if (!fin(hr)) continue;
-                const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
-                if (cls) {
-                  const uint32_t key =
-                      tl_key(l1, l2, cs, ds, wt, p1.label, p2.label, r1.label, r2.label);
-                  const int64_t b3 = wv + hc + fx(T.interior[5] + T.ninio);
-                  FOR_T({
-                    upd(qv, qk, b3 + fx(T.mm23[t][p1.label * 4 + r2.label]), key);
-                    TERM(8);
-                  });
-                } else {
+    const int lcs = F.ls(lc), lds = F.ls(ld), lc1s = F.ls(lc - 1), ld1s = F.ls(ld + 1);
+    const int pi0 = F.fi_off[lcs], npi = F.fi_off[F.ls(lc + 1)] - pi0;
+    const int ro0 = F.fo_off[lds], nro = F.fo_off[F.ls(ld + 1)] - ro0;
+    for (int k = sub; k < npi * nro; k += G) {
+      const int kp = k / nro, kr = k - kp * nro;
+      const SdFlatEdge p2 = F.fi[pi0 + kp], r1 = F.fo[ro0 + kr];
+      const int cs = p2.v - lcs, ds = r1.v - lds;
+      const int w = p2.wl >> 2, lL = p2.wl & 3, u = r1.wl >> 2, fR = r1.wl & 3;
+      int64_t vv[6];
+      int64_t wv = SD_INF;
+      int wt = 7;
+      if (cls == 0) {
+        F.v6(F.cs(lc, cs, ld, ds), vv);
+        if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
+          continue;
+      } else {
+        const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR];
+        if (!fin(pk)) continue;
+        wv = pk >> 3;
+        wt = (int)(pk & 7);
+      }
+      for (int a = 0; a < nox; a++) {
+        const SdEdge p1 = F.out(x, a);
+        const int64_t hl = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lc1s);
+        if (!fin(hl)) continue;
+        for (int b2 = 0; b2 < niy; b2++) {
+          const SdEdge r2 = F.in(y, b2);
+          const int64_t hr = F.Hh(ld + 1, u - ld1s, ly - 1, r2.other - ly1s);
+          if (!fin(hr)) continue;
+          const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
+          const int fL = p1.label, lR = r2.label;
+          if (cls) {
+            upd6<COUNT>(qv, qk, tm, wv + hc + fx(T.interior[5] + T.ninio),
+                        tl_key(l1, l2, cs, ds, wt, fL, lL, fR, lR), 8, ops,
+                        [&](int t) { return T.mm23[t][fL * 4 + lR]; });
+          } else {
+            const int idx = fL * 64 + lL * 16 + fR * 4 + lR;
 #pragma unroll
-                  for (int ti = 0; ti < 6; ti++) {
-                    if (!fin(vv[ti])) continue;
-                    const int s = c_rev[ti];
-                    const uint32_t key =
-                        tl_key(2, 2, cs, ds, ti, p1.label, p2.label, r1.label, r2.label);
-                    FOR_T({
-                      upd(qv, qk,
-                          vv[ti] + hc +
-                              fx(P.int22[t][s][p1.label * 64 + p2.label * 16 + r1.label * 4 +
-                                               r2.label]),
-                          key);
-                      TERM(8);
-                    });
-                  }
-                }
-              }
+            for (int ti = 0; ti < 6; ti++) {
+              if (!fin(vv[ti])) continue;
+              const int s = c_rev[ti];
+              upd6<COUNT>(qv, qk, tm, vv[ti] + hc, tl_key(2, 2, cs, ds, ti, fL, lL, fR, lR), 8,
+                          ops, [&](int t) { return P.int22[t][s][idx]; });
             }
           }
         }
       }
-    return;
-  }
-  if (it == 122) {  // generic internal loops: mismatch edges + IL two spans below
-    if (g < 11) return;
-    const int l1s = F.ls(lx + 1), l2s = F.ls(ly - 1);
-    for (int a = 0; a < F.nout(x); a++) {
-      const SdEdge e1 = F.out(x, a);
-      for (int b = 0; b < F.nin(y); b++) {
-        const SdEdge e2 = F.in(y, b);
-        const int r = F.rs(lx + 1, e1.other - l1s, ly - 1, e2.other - l2s);
-        const int64_t il = D.IL[r];
-        if (!fin(il)) continue;
-        const uint32_t key = (1u << 25) | D.ILk[r] | ((uint32_t)e1.label << 6) | (uint32_t)e2.label;
-        const int64_t base = il + e1.cost + e2.cost;
-        FOR_T({
-          upd(qv, qk, base + fx(T.mmI[t][e1.label * 4 + e2.label]), key);
-          TERM(3);
-        });
-      }
     }
-    return;
   }
-  // multiloop closed by the pair
-  if (g < 10) return;
-  const int64_t s2 = D.S2[F.cs(lx, sx, ly, sy)];
-  if (!fin(s2)) return;
-  FOR_T({
-    upd(qv, qk, s2 + fx(T.mlclosing + T.mlintern + T.au[t]), KEY_ML);
-    TERM(1);
-  });
+  // ---- generic internal loops: mismatch edges + the IL table two spans below ----
+  if (g >= 11)
+    for (int k = sub; k < nox * niy; k += G) {
+      const int a = k / niy, b = k - a * niy;
+      const SdEdge e1 = F.out(x, a), e2 = F.in(y, b);
+      const int r = F.rs(lx + 1, e1.other - lx1s, ly - 1, e2.other - ly1s);
+      const int64_t il = D.IL[r];
+      if (!fin(il)) continue;
+      const int idx = e1.label * 4 + e2.label;
+      upd6<COUNT>(qv, qk, tm, il + e1.cost + e2.cost,
+                  (1u << 25) | D.ILk[r] | ((uint32_t)e1.label << 6) | (uint32_t)e2.label, 3, ops,
+                  [&](int t) { return T.mmI[t][idx]; });
+    }
+  // ---- multiloop closed by the pair ----
+  if (g >= 10 && sub == G - 1) {
+    const int64_t s2 = D.S2[F.cs(lx, sx, ly, sy)];
+    if (fin(s2))
+      upd6<COUNT>(qv, qk, tm, s2 + fx(T.mlclosing + T.mlintern), KEY_ML, 1, ops,
+                  [&](int t) { return T.au[t]; });
+  }
 }
 
 // (l1', l2') pairs of the generic internal loops, l1'+l2' in [2, 26]
 constexpr int IL_PAIRS = 375;
 
 // ---------------------------------------------------------------------------
-// the span kernel: G threads per layer pair (i, i+g).  With G = 1 a warp
-// takes 32 layer pairs of one residue class mod 3 (so its lanes see the same
-// layer types and take the same branches); otherwise consecutive groups take
-// consecutive layer pairs.
+// the span kernel: a group of G threads (G = 8, 16 or 32) per layer pair
+// (i, i+g); consecutive groups take consecutive layer pairs.
 // ---------------------------------------------------------------------------
 template <int G>
 struct FillShape {
-  static constexpr int threads = G == 1 ? 96 : 128;
+  static constexpr int threads = 128;
   static constexpr int pairs = threads / G;
-  __device__ static int pair_index(int bx) {
-    if (G == 1) {
-      const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-      return bx * 96 + warp + 3 * lane;
-    }
-    return bx * pairs + (int)threadIdx.x / G;
-  }
+  __device__ static int pair_index(int bx) { return bx * pairs + (int)threadIdx.x / G; }
 };
 
+
 template <int G, bool COUNT>
-__global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::threads)
+__global__ void __launch_bounds__(128, 4)
     k_fill_span(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp, int g,
                 int nact, int items, const int32_t *__restrict__ cpre,
                 unsigned long long *ops_out) {
   constexpr int NT = FillShape<G>::threads;
   __shared__ SmallTables T;
   __shared__ uint16_t s_il[IL_PAIRS];
+  __shared__ GapStage s_gap[FillShape<G>::pairs];
   {
     const int32_t *src[] = {&Pp->stack[0][0], &Pp->mmH[0][0], &Pp->bulge[0], &Pp->au[0],
                             &Pp->ninio};
@@ -730,6 +713,11 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
   F.H = D.H;
   F.Hk = D.Hk;
   F.V = D.V;
+  F.lay = D.layer;
+  F.fo = D.fo;
+  F.fo_off = D.fo_off;
+  F.fi = D.fi;
+  F.fi_off = D.fi_off;
   int a0 = 0, wa = 0, b0 = 0, wb = 0;
   if (active) {
     a0 = F.ls(i);
@@ -742,6 +730,40 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
   const int64_t mlb = fx(T.mlbase);
   const int js = active ? F.ls(j - 1) : 0;  // first state on layer j-1
   const int i1s = active ? F.ls(i + 1) : 0;
+  GapStage &GS = s_gap[threadIdx.x / G];
+  {
+    const int lmax = min(SD_GAPW - 1, g - 1);  // spans below g only (this span is not filled yet)
+    for (int q = sub; q < SD_GAPW * 4; q += G) {
+      const int l = q >> 2, c = (q >> 1) & 1, sn = q & 1;
+      int64_t vl = SD_INF, vr = SD_INF;
+      uint8_t kl = 0, kr = 0;
+      if (active && l <= lmax) {
+        if (sn < wa && c < F.w(i + l)) {
+          if (l == 0) {
+            vl = c == sn ? 0 : SD_INF;
+          } else {
+            const int h = F.cs(i, sn, i + l, c);
+            vl = F.H[h];
+            kl = F.Hk[h];
+          }
+        }
+        if (sn < wb && c < F.w(j - l)) {
+          if (l == 0) {
+            vr = c == sn ? 0 : SD_INF;
+          } else {
+            const int h = F.cs(j - l, c, j, sn);
+            vr = F.H[h];
+            kr = F.Hk[h];
+          }
+        }
+      }
+      GS.hl[l][c * 2 + sn] = vl;
+      GS.hr[l][c * 2 + sn] = vr;
+      GS.hlk[l][c * 2 + sn] = kl;
+      GS.hrk[l][c * 2 + sn] = kr;
+    }
+    __syncwarp();
+  }
 
   int64_t Bs[SD_SLOTS], PSs[SD_SLOTS];
 #pragma unroll
@@ -758,7 +780,10 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
     if (ok) {
       int64_t hv = SD_INF;
       uint32_t hk = KEY_NONE;
-      for (int k = 0; k < F.nin(b); k++) {
+      const int nib = F.nin(b);
+#pragma unroll
+      for (int k = 0; k < SD_MAXIN; k++) {
+        if (k >= nib) break;
         const SdEdge e = F.in(b, k);
         int64_t hp;
         int f;
@@ -808,64 +833,30 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
         D.Ihk[rcell + s] = ik;
       }
     }
-    // IL: generic internal loops l1 = l1'+2, l2 = l2'+2 around (a,b)
-    {
-      int64_t lv = SD_INF;
-      uint32_t lk = KEY_NONE;
-      if (ok && g >= 9) {
-        for (int q = sub; q < IL_PAIRS; q += G) {
-          const int pr = s_il[q];
-          const int l1p = pr & 31, l2p = pr >> 5;
-          const int lc = i + l1p, ld = j - l2p;
-          if (ld - lc < 7) continue;
-          const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
-          const int64_t e = fx(T.interior[l1p + l2p + 4] + min(T.maxninio, T.ninio * dd));
-          const uint32_t kl = ((uint32_t)(l1p + l2p + 4) << 20) | ((uint32_t)(l1p + 2) << 15);
-          const int wc = F.w(lc), wd = F.w(ld);
-          for (int cs = 0; cs < wc; cs++) {
-            const int64_t hl = F.Hh(i, sa, lc, cs);
-            if (!fin(hl)) continue;
-            for (int ds = 0; ds < wd; ds++) {
-              const int64_t hr = F.Hh(ld, ds, j, sb);
-              if (!fin(hr)) continue;
-              const int r = F.rs(lc, cs, ld, ds);
-              const int64_t v = D.Ihat[r];
-              if (!fin(v)) continue;
-              upd(lv, lk, hl + v + hr + e, kl | D.Ihk[r]);
-              TERM(3);
-            }
-          }
-        }
-      }
-      seg_lexmin<G>(lv, lk);
-      settle(lv, lk);
-      if (ok && sub == 0) {
-        D.IL[rcell + s] = lv;
-        D.ILk[rcell + s] = lk;
-      }
-    }
     // typed closed values (every thread of the group) and Eq. (branch)
     int64_t vv[6];
     {
+      const int oma = ok ? D.out_mask[a] : 0, nib = ok ? F.nin(b) : 0;
       int64_t B = SD_INF;
       uint32_t Bk = KEY_NONE;
 #pragma unroll
       for (int t = 0; t < 6; t++) {
         int64_t v = SD_INF;
         uint32_t vk = KEY_NONE;
-        if (ok && g >= 5) {
-          for (int k1 = 0; k1 < F.nout(a); k1++) {
-            const SdEdge e1 = F.out(a, k1);
-            if (e1.label != c_pair5[t]) continue;
-            for (int k2 = 0; k2 < F.nin(b); k2++) {
-              const SdEdge e2 = F.in(b, k2);
-              if (e2.label != c_pair3[t]) continue;
-              const int r = F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t;
-              const int64_t q = D.Q[r];
-              if (!fin(q)) continue;
-              upd(v, vk, q + e1.cost + e2.cost, ((uint32_t)k2 << 27) | D.Qk[r]);
-              TERM(2);
-            }
+        // the out-edge of a labelled with the pair's 5' nucleotide (a DFA has
+        // at most one; out-edges are stored by label)
+        const int l5 = c_pair5[t];
+        if (ok && g >= 5 && ((oma >> l5) & 1)) {
+          const SdEdge e1 = F.out(a, __popc(oma & ((1 << l5) - 1)));
+          const int l3 = c_pair3[t];
+          for (int k2 = 0; k2 < nib; k2++) {
+            const SdEdge e2 = F.in(b, k2);
+            if (e2.label != l3) continue;
+            const int r = F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t;
+            const int64_t q = D.Q[r];
+            if (!fin(q)) continue;
+            upd(v, vk, q + e1.cost + e2.cost, ((uint32_t)k2 << 27) | D.Qk[r]);
+            TERM(2);
           }
         }
         settle(v, vk);
@@ -899,20 +890,72 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
             if (((im >> li) & 1) && ((om >> lo) & 1))
               best_inner(vv, tab == 0 ? T.mm1n : tab == 1 ? T.mm23 : T.mmI, lo * 4 + li, bv, bt);
           } else {
-#pragma unroll
-            for (int ti = 0; ti < 6; ti++)
-              if (fin(vv[ti])) {
-                const int64_t v = vv[ti] + fx(T.au[c_rev[ti]]);
-                if (v < bv) {
-                  bv = v;
-                  bt = ti;
-                }
-              }
+            best_au(vv, T.au, bv, bt);
           }
         }
         Wc[q] = fin(bv) ? bv * 8 + bt : SD_INF;
       }
     }
+  }
+  // IL: generic internal loops (l1 = l1'+2, l2 = l2'+2) around every slot of the
+  // layer pair at once: each inner cell (c,d) is read once for all slots, the
+  // gap values of both ends come from the staged vectors
+  if (g >= 9) {
+    int64_t lv[SD_SLOTS];
+    uint32_t lk[SD_SLOTS];
+#pragma unroll
+    for (int s = 0; s < SD_SLOTS; s++) {
+      lv[s] = SD_INF;
+      lk[s] = KEY_NONE;
+    }
+    if (active)
+      for (int q = sub; q < IL_PAIRS; q += G) {
+        const int pr = s_il[q];
+        const int l1p = pr & 31, l2p = pr >> 5;
+        const int lc = i + l1p, ld = j - l2p;
+        if (ld - lc < 7) continue;
+        const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
+        const int64_t e = fx(T.interior[l1p + l2p + 4] + min(T.maxninio, T.ninio * dd));
+        const uint32_t kl = ((uint32_t)(l1p + l2p + 4) << 20) | ((uint32_t)(l1p + 2) << 15);
+        const int wc = F.w(lc), wd = F.w(ld);
+        for (int cs = 0; cs < wc; cs++) {
+          const int64_t hl0 = GS.hl[l1p][cs * 2], hl1 = GS.hl[l1p][cs * 2 + 1];
+          if (!fin(hl0) && !fin(hl1)) continue;
+          for (int ds = 0; ds < wd; ds++) {
+            const int64_t hr0 = GS.hr[l2p][ds * 2], hr1 = GS.hr[l2p][ds * 2 + 1];
+            if (!fin(hr0) && !fin(hr1)) continue;
+            const int r = F.rs(lc, cs, ld, ds);
+            const int64_t v = D.Ihat[r];
+            if (!fin(v)) continue;
+            const uint32_t key = kl | D.Ihk[r];
+            const int64_t ve = v + e;
+#pragma unroll
+            for (int s = 0; s < SD_SLOTS; s++) {
+              const int64_t h1 = (s >> 1) ? hl1 : hl0, h2 = (s & 1) ? hr1 : hr0;
+              if (fin(h1) && fin(h2)) {
+                upd(lv[s], lk[s], h1 + ve + h2, key);
+                TERM(3);
+              }
+            }
+          }
+        }
+      }
+#pragma unroll
+    for (int s = 0; s < SD_SLOTS; s++) {
+      seg_lexmin<G>(lv[s], lk[s]);
+      settle(lv[s], lk[s]);
+      if (active && (s >> 1) < wa && (s & 1) < wb && sub == s % G) {
+        D.IL[rcell + s] = lv[s];
+        D.ILk[rcell + s] = lk[s];
+      }
+    }
+  } else if (active && sub == 0) {
+#pragma unroll
+    for (int s = 0; s < SD_SLOTS; s++)
+      if ((s >> 1) < wa && (s & 1) < wb) {
+        D.IL[rcell + s] = SD_INF;
+        D.ILk[rcell + s] = KEY_NONE;
+      }
   }
   // Eq. (sparse2) for every slot: edge extensions, then splits at retained
   // candidates (the group splits the candidate list)
@@ -1000,36 +1043,36 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
       }
       D.cand_cnt[b] = cnt;
     }
-  // closed-interior values for the pairs two spans up
+  __syncwarp();  // the stack option reads V of this cell, written by another thread
+  // closed-interior values for the pairs two spans up, all outer types at once
 #pragma unroll 1
   for (int s = 0; s < SD_SLOTS; s++) {
     const int sa = s / SD_W, sb = s % SD_W;
     const bool ok = active && sa < wa && sb < wb;
     const int x = a0 + sa, y = b0 + sb;
-    int tmask = 0;
+    // outer types that can close (x, y); the same for all threads of a group
+    int tm = 0;
     if (ok) {
       const int im = D.in_mask[x], om = D.out_mask[y];
 #pragma unroll
       for (int t = 0; t < 6; t++)
-        if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tmask |= 1 << t;
+        if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tm |= 1 << t;
     }
-    // one outer type at a time (the types of a layer pair are the same for
-    // all threads of its group); types that cannot close (x, y) stay +inf
-#pragma unroll 1
+    int64_t qv[6];
+    uint32_t qk[6];
+#pragma unroll
     for (int t = 0; t < 6; t++) {
-      int64_t qv = SD_INF;
-      uint32_t qk = KEY_NONE;
-      if ((tmask >> t) & 1)
-        for (int cl = 0; cl < Q_CLASSES; cl++) {
-          const int st = c_qclass[cl][0], cnt = c_qclass[cl][1], rot = c_qclass[cl][2] % G;
-          for (int k = (sub - rot + G) % G; k < cnt; k += G)
-            q_item<COUNT>(F, D, P, T, st + k, x, y, i, sa, j, sb, t, qv, qk, ops);
-        }
-      if (__any_sync(FULL, (tmask >> t) & 1)) seg_lexmin<G>(qv, qk);
-      settle(qv, qk);
-      if (ok && sub == 0) {
-        D.Q[(int64_t)(rcell + s) * 6 + t] = qv;
-        D.Qk[(int64_t)(rcell + s) * 6 + t] = qk;
+      qv[t] = SD_INF;
+      qk[t] = KEY_NONE;
+    }
+    if (tm) q_slot<G, COUNT>(F, D, P, T, sub, x, y, i, sa, j, sb, tm, qv, qk, ops, GS);
+#pragma unroll
+    for (int t = 0; t < 6; t++) {
+      if (__any_sync(FULL, (tm >> t) & 1)) seg_lexmin<G>(qv[t], qk[t]);
+      settle(qv[t], qk[t]);
+      if (ok && sub == t % G) {
+        D.Q[(int64_t)(rcell + s) * 6 + t] = qv[t];
+        D.Qk[(int64_t)(rcell + s) * 6 + t] = qk[t];
       }
     }
   }
@@ -1508,7 +1551,7 @@ __global__ void k_count(const SdDesign *__restrict__ designs, unsigned long long
 template <int G, bool COUNT>
 void launch_fill_g(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
                    const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
-  constexpr int per_block = G == 1 ? 96 : FillShape<G>::pairs;
+  constexpr int per_block = FillShape<G>::pairs;
   int nact = count;
   int64_t cp = 0;
   for (int d = 0; d < count; d++) cp += ns[d] + 1;
@@ -1530,8 +1573,8 @@ template <bool COUNT>
 int launch_fill(int G, const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
                 const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
   switch (G) {
-    case 1: launch_fill_g<1, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
     case 8: launch_fill_g<8, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
+    case 16: launch_fill_g<16, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
     case 32: launch_fill_g<32, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
     default: return -1;
   }

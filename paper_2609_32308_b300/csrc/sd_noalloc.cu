@@ -53,6 +53,8 @@ struct FixedLattice {
   uint8_t out_cnt[kMaxStates], in_cnt[kMaxStates], in_mask[kMaxStates], out_mask[kMaxStates];
   int32_t hp[kMaxNt + 1];
   int64_t cand_off[kMaxStates];
+  SdFlatEdge fo[kMaxStates * SD_MAXOUT], fi[kMaxStates * SD_MAXOUT];
+  int32_t fo_off[kMaxStates + 1], fi_off[kMaxStates + 1];
 };
 FixedLattice g_lat;
 
@@ -204,6 +206,10 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.in_mask = (uint8_t *)take(N);
   d.out_mask = (uint8_t *)take(N);
   d.hp_len = (int32_t *)take((n + 1) * 4);
+  d.fo = (SdFlatEdge *)take((L.E > 0 ? L.E : 1) * sizeof(SdFlatEdge));
+  d.fo_off = (int32_t *)take((N + 1) * 4);
+  d.fi = (SdFlatEdge *)take((L.E > 0 ? L.E : 1) * sizeof(SdFlatEdge));
+  d.fi_off = (int32_t *)take((N + 1) * 4);
   d.H = (int64_t *)take(ncell * SD_SLOTS * 8);
   d.Hk = (uint8_t *)take(ncell * SD_SLOTS);
   d.V = (int64_t *)take(ncell * SD_SLOTS * 6 * 8);
@@ -256,6 +262,7 @@ extern "C" int sd_design_noalloc(const sd_energy *energy, const char *protein,
   rc = sd_internal_range_check(energy, L.n, L.qmax_sum);
   if (rc != SD_OK) return rc;
   for (int Lh = 0; Lh <= L.n; Lh++) L.hp[Lh] = sd_internal_hairpin_len(energy, Lh);
+  sd_internal_flatten(L.N, L.out, L.out_cnt, L.in, L.in_cnt, L.fo, L.fo_off, L.fi, L.fi_off);
   // set-up, once per device, with that device current
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SD_ECUDA;
@@ -276,7 +283,11 @@ extern "C" int sd_design_noalloc(const sd_energy *energy, const char *protein,
       !h2d((void *)d.in, L.in, N * SD_MAXIN * sizeof(SdEdge)) ||
       !h2d((void *)d.in_cnt, L.in_cnt, N) || !h2d((void *)d.in_mask, L.in_mask, N) ||
       !h2d((void *)d.out_mask, L.out_mask, N) || !h2d((void *)d.hp_len, L.hp, (n + 1) * 4) ||
-      !h2d((void *)d.cand_off, L.cand_off, N * 8) || !h2d(rec, &d, sizeof(SdDesign)))
+      !h2d((void *)d.cand_off, L.cand_off, N * 8) ||
+      !h2d((void *)d.fo, L.fo, L.E * sizeof(SdFlatEdge)) ||
+      !h2d((void *)d.fi, L.fi, L.E * sizeof(SdFlatEdge)) ||
+      !h2d((void *)d.fo_off, L.fo_off, (N + 1) * 4) ||
+      !h2d((void *)d.fi_off, L.fi_off, (N + 1) * 4) || !h2d(rec, &d, sizeof(SdDesign)))
     return SD_ECUDA;
   int64_t launches = 0;
   int32_t *cpre = (int32_t *)((char *)counts + 256);  // the 2-int block carved after counts

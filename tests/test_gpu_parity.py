@@ -191,7 +191,7 @@ def test_full_size_design_properties(sd, E1, par1, A, lam):
     assert 0 < r["Z"] <= r["finite_direct"]
 
 
-@pytest.mark.parametrize("group", [1, 32])
+@pytest.mark.parametrize("group", [8, 16, 32])
 def test_every_group_size_gives_the_oracle_tables(sd, E1, par1, group):
     """The fill's threads-per-layer-pair choice changes speed, never results."""
     prot = inputs.random_protein(35, 31)
