@@ -155,8 +155,9 @@ int sd_plan_phase_times(const sd_plan *plan, float *ms3);
  * does, but without the exterior pass and the traceback. */
 int sd_plan_count_ops(sd_plan *plan, int64_t *ops);
 
-/* Threads cooperating on one layer pair in the fill: 8, 16 or 32 (default
- * 32); anything else is SD_EINVAL.  Results do not depend on it; speed does.
+/* Threads cooperating on one layer pair in the fill: 8, 16 or 32; anything
+ * else is SD_EINVAL.  The default is 8 when the designs of the plan have at
+ * least 16,384 nucleotides in total (many layer pairs per span), else 32.  Results do not depend on it; speed does.
  * sd_plan_autotune runs the plan once per candidate (synchronously, legacy
  * default stream), keeps the fastest and writes the three fill times (ms, in
  * the order 8, 16, 32) to ms3 (may be NULL). */
@@ -238,8 +239,11 @@ int sd_plan_create_predicted(const sd_energy *energy, sd_predictor *pred, double
                              const char *const *proteins, const double *codon_weights,
                              int weights_shared, const double *lambdas, sd_plan **out,
                              int *item_status);
-/* Candidate-list entries reserved by a plan (all items). */
+/* Candidate-list entries reserved by a plan (all items), and the entries the
+ * same items would reserve with worst-case room (every state at least five
+ * layers before the list's end state).  NULL plan: 0. */
 int64_t sd_plan_candidate_room(const sd_plan *plan);
+int64_t sd_plan_candidate_room_worst(const sd_plan *plan);
 
 #ifdef __cplusplus
 }

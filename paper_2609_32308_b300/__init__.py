@@ -80,6 +80,8 @@ def lib():
         L.sd_plan_retention.argtypes = [P, I, P]
         L.sd_plan_candidate_room.argtypes = [P]
         L.sd_plan_candidate_room.restype = ctypes.c_int64
+        L.sd_plan_candidate_room_worst.argtypes = [P]
+        L.sd_plan_candidate_room_worst.restype = ctypes.c_int64
         L.sd_plan_create_predicted.argtypes = [P, P, D, I, P, P, I, P, ctypes.POINTER(P), P]
         L.sd_pred_create.argtypes = [ctypes.c_uint64, ctypes.POINTER(P)]
         L.sd_pred_free.argtypes = [P]
@@ -325,6 +327,10 @@ class Plan:
     @property
     def candidate_room(self) -> int:
         return int(lib().sd_plan_candidate_room(self.handle))
+
+    @property
+    def candidate_room_worst(self) -> int:
+        return int(lib().sd_plan_candidate_room_worst(self.handle))
 
     def size(self, item: int):
         n, N, E = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

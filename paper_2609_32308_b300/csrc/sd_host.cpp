@@ -600,6 +600,9 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
       cpre[r + 1] = cpre[r] + p->ns[r] + 1;
     }
     p->cpre_host = cpre;
+    // default fill group: 8 threads per layer pair when a span holds many
+    // layer pairs (a large batch), else 32 (sd_plan_autotune measures)
+    p->group = cpre.back() >= 16384 ? 8 : 32;
   }
   if (!p->hdesigns.empty()) {
     if (cudaMalloc(&p->arena, total) != cudaSuccess) {
@@ -947,6 +950,15 @@ extern "C" int64_t sd_plan_candidate_room(const sd_plan *p) {
   for (const auto &it : p->items)
     if (it.status == SD_OK)
       for (int v = 0; v < it.L.N; v++) total += room(it.L, v);
+  return total;
+}
+
+extern "C" int64_t sd_plan_candidate_room_worst(const sd_plan *p) {
+  if (!p) return 0;
+  int64_t total = 0;
+  for (const auto &it : p->items)
+    if (it.status == SD_OK)
+      for (int v = 0; v < it.L.N; v++) total += worst_room(it.L, v);
   return total;
 }
 

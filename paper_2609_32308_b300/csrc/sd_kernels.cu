@@ -1615,6 +1615,17 @@ extern "C" int sd_k_count_ops(const SdDesign *d_designs, int count, const int *n
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
+// An event record that also becomes an event-record node when the stream is
+// being captured into a graph (a plain record there is only a capture
+// dependency and would not fire when the graph is replayed).
+static void record(void *ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags((cudaEvent_t)ev, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord((cudaEvent_t)ev, st);
+}
+
 extern "C" int sd_k_run(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
                         const SdParams *d_params, void *stream, int64_t *launches,
                         void *const *events, int group) {
@@ -1624,13 +1635,13 @@ extern "C" int sd_k_run(const SdDesign *d_designs, int count, const int *ns, con
     return 0;
   }
   k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
-  if (events) cudaEventRecord((cudaEvent_t)events[0], st);
+  if (events) record(events[0], st);
   if (launch_fill<false>(group, d_designs, count, ns, d_cpre, d_params, st, nullptr)) return -1;
-  if (events) cudaEventRecord((cudaEvent_t)events[1], st);
+  if (events) record(events[1], st);
   k_exterior<<<count, 256, 0, st>>>(d_designs, d_params);
-  if (events) cudaEventRecord((cudaEvent_t)events[2], st);
+  if (events) record(events[2], st);
   k_traceback<<<count, 128, 0, st>>>(d_designs, d_params);
-  if (events) cudaEventRecord((cudaEvent_t)events[3], st);
+  if (events) record(events[3], st);
   if (launches) *launches = (int64_t)ns[0] + 3;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

@@ -220,3 +220,36 @@ def test_graph_replay_of_a_mixed_batch(sd, E1, par1):
         res = plan.results()
         for (p, w, lam), r in zip(batch, res):
             compare_design(r, oracle.run(par1, p, w, lam), lam)
+
+
+def test_phase_times_under_graph_replay(sd, E1):
+    """Phase events recorded inside the captured graph fire on every replay."""
+    batch = inputs.protein_batch([40, 25], seed=7)
+    plan = sd.Plan(E1, [b[0] for b in batch], np.stack([b[1] for b in batch]),
+                   [b[2] for b in batch])
+    plan.set_graph(True)
+    plan.set_timing(True)
+    for _ in range(2):
+        plan.run()
+        ms = plan.phase_times()
+        assert len(ms) == 3 and all(x > 0 for x in ms)
+    assert all(r["status"] == 0 for r in plan.results())
+    plan.free()
+
+
+def test_autotune_then_graph(sd, E1):
+    """The autotuner's timed runs (no graph) and a timed graph replay after it."""
+    batch = inputs.protein_batch([30, 30, 20], seed=8)
+    args = ([b[0] for b in batch], np.stack([b[1] for b in batch]), [b[2] for b in batch])
+    plan = sd.Plan(E1, *args)
+    tune = plan.autotune()
+    assert sorted(tune) == [8, 16, 32] and all(v > 0 for v in tune.values())
+    assert plan.group in (8, 16, 32)
+    plan.set_graph(True)
+    plan.set_timing(True)
+    plan.run()
+    assert all(x > 0 for x in plan.phase_times())
+    base = sd.sd_design_batch(E1, *args)
+    got = plan.results()
+    assert [(r["mrna"], r["energy"]) for r in got] == [(r["mrna"], r["energy"]) for r in base]
+    plan.free()
