@@ -54,6 +54,11 @@ def parse():
     ap.add_argument("--cpu-sample-aa", type=int, default=80)
     ap.add_argument("--no-predictor", action="store_true",
                     help="worst-case candidate room instead of the predictor's")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling case: build the batch, run it once with --group, read "
+                         "the results; no timing and no JSON line")
+    ap.add_argument("--group", type=int, default=8, help="fill group for --once")
+    ap.add_argument("--length", type=int, default=LENGTH, help="protein length for --once")
     return ap.parse_args()
 
 
@@ -122,11 +127,32 @@ class Clocks:
                 "samples": len(rows)}
 
 
-def workload(batch: int, rank: int):
+def shard_seeds(batch: int, rank: int) -> list:
+    """Seeds of the proteins rank `rank` designs: disjoint across ranks, so N
+    ranks design N * batch distinct proteins (weak scaling, no exchange)."""
+    return [100000 + rank * batch + k for k in range(batch)]
+
+
+def max_over_ranks(x: float, dist=None, device: str = "cpu") -> float:
+    """The step time of the whole job: the slowest rank's."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(designs_per_rank: int, world: int, steps: int, elapsed_max: float) -> float:
+    """Whole-job designs/s: all ranks' designs over the slowest rank's time."""
+    return designs_per_rank * world * steps / elapsed_max
+
+
+def workload(batch: int, rank: int, length: int = LENGTH):
     from paper_2609_32308_b300 import inputs
     import numpy as np
-    seeds = [100000 + rank * batch + k for k in range(batch)]
-    prots = [inputs.random_protein(LENGTH, s) for s in seeds]
+    seeds = shard_seeds(batch, rank)
+    prots = [inputs.random_protein(length, s) for s in seeds]
     ws = np.stack([inputs.random_codon_weights(s) for s in seeds])
     return prots, ws, [LAMBDA] * batch
 
@@ -202,10 +228,30 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_once(args):
+    """One untimed pass of the batched plan (fixed launch order: clear, one fill
+    launch per span, exterior, traceback) for a profiler to capture."""
+    import paper_2609_32308_b300 as sd
+    E = sd.sd_load_energy(energy_path())
+    prots, ws, lams = workload(args.batch, 0, args.length)
+    plan = sd.Plan(E, prots, ws, lams)
+    plan.group = args.group
+    plan.run()
+    res = plan.results()
+    assert all(r["status"] == 0 for r in res)
+    print(json.dumps({"once": True, "batch": args.batch, "length_aa": args.length,
+                      "group": args.group, "energy0": res[0]["energy"],
+                      "device_gb": plan.device_bytes / 1e9}), flush=True)
+    plan.free()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.once:
+        run_once(args)
         return
     import torch
     import numpy as np
@@ -223,12 +269,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def ranks_max(x: float) -> float:
+        return max_over_ranks(x, dist, "cuda")
 
     E = sd.sd_load_energy(energy_path())
     prots, ws, lams = workload(args.batch, rank)
@@ -267,7 +309,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     clocks = clk.summary()
-    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1000.0)
+    elapsed = ranks_max(t0.elapsed_time(t1) / 1000.0)
     # ---- everything below is outside the timed region ----
     res = plan.results()
     assert all(r["status"] == 0 for r in res), [r["status"] for r in res]
@@ -275,8 +317,7 @@ def main():
     assert sum(r["regrows"] for r in res) == regrows
     room, room_worst = plan.candidate_room, plan.candidate_room_worst
     cells = sum(r["retained_cells"] for r in res)
-    designs = args.batch * world * args.steps
-    value = designs / elapsed
+    value = job_rate(args.batch, world, args.steps, elapsed)
     cell_rate = cells * world * args.steps / elapsed
     launches = plan.launches * args.steps
     phase = [statistics.mean(x[k] for x in phases) for k in range(3)]
@@ -298,7 +339,7 @@ def main():
         plain.run(stream)
     p1.record(stream)
     torch.cuda.synchronize()
-    plain_elapsed = max_over_ranks(p0.elapsed_time(p1) / 1000.0)
+    plain_elapsed = ranks_max(p0.elapsed_time(p1) / 1000.0)
     plain_value = world * args.steps / plain_elapsed
     plain.free()
 
@@ -309,7 +350,7 @@ def main():
     for _ in range(args.steps):
         out = sd.sd_design_batch(E, prots, ws, lams)
     torch.cuda.synchronize()
-    e_elapsed = max_over_ranks(time.perf_counter() - e0)
+    e_elapsed = ranks_max(time.perf_counter() - e0)
     assert all(r["status"] == 0 for r in out)
     # bytes the library copies per step: lattices and design records up,
     # sequences, structures, traceback words, optimum and counters down

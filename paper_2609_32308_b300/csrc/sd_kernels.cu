@@ -660,6 +660,7 @@ __global__ void __launch_bounds__(128, 4)
   constexpr int NT = FillShape<G>::threads;
   __shared__ SmallTables T;
   __shared__ uint16_t s_il[IL_PAIRS];
+  __shared__ int32_t s_ile[IL_PAIRS];  // size and asymmetry energy of each (l1', l2')
   __shared__ GapStage s_gap[FillShape<G>::pairs];
   {
     const int32_t *src[] = {&Pp->stack[0][0], &Pp->mmH[0][0], &Pp->bulge[0], &Pp->au[0],
@@ -677,6 +678,8 @@ __global__ void __launch_bounds__(128, 4)
       for (int a = 0; a < l1p; a++) r += (SD_MAXTWO - 4 - a + 1) - (a < 2 ? 2 - a : 0);
       r += l2p - (l1p < 2 ? 2 - l1p : 0);
       s_il[r] = (uint16_t)(l1p | (l2p << 5));
+      const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
+      s_ile[r] = Pp->interior[l1p + l2p + 4] + min(Pp->maxninio, Pp->ninio * dd);
     }
   }
   __syncthreads();
@@ -914,17 +917,19 @@ __global__ void __launch_bounds__(128, 4)
         const int l1p = pr & 31, l2p = pr >> 5;
         const int lc = i + l1p, ld = j - l2p;
         if (ld - lc < 7) continue;
-        const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
-        const int64_t e = fx(T.interior[l1p + l2p + 4] + min(T.maxninio, T.ninio * dd));
+        const int64_t e = fx(s_ile[q]);
         const uint32_t kl = ((uint32_t)(l1p + l2p + 4) << 20) | ((uint32_t)(l1p + 2) << 15);
-        const int wc = F.w(lc), wd = F.w(ld);
-        for (int cs = 0; cs < wc; cs++) {
+        const int rb = (((ld - lc) & (SD_RING - 1)) * (n + 1) + lc) * SD_SLOTS;
+        // slots beyond a layer's width have +inf staged gap values
+#pragma unroll
+        for (int cs = 0; cs < SD_W; cs++) {
           const int64_t hl0 = GS.hl[l1p][cs * 2], hl1 = GS.hl[l1p][cs * 2 + 1];
           if (!fin(hl0) && !fin(hl1)) continue;
-          for (int ds = 0; ds < wd; ds++) {
+#pragma unroll
+          for (int ds = 0; ds < SD_W; ds++) {
             const int64_t hr0 = GS.hr[l2p][ds * 2], hr1 = GS.hr[l2p][ds * 2 + 1];
             if (!fin(hr0) && !fin(hr1)) continue;
-            const int r = F.rs(lc, cs, ld, ds);
+            const int r = rb + cs * SD_W + ds;
             const int64_t v = D.Ihat[r];
             if (!fin(v)) continue;
             const uint32_t key = kl | D.Ihk[r];

@@ -191,6 +191,49 @@ def test_full_size_design_properties(sd, E1, par1, A, lam):
     assert 0 < r["Z"] <= r["finite_direct"]
 
 
+def test_longest_config_properties_and_footprint(sd, E1, par1):
+    """1,976 aa (5,928 nt) at lambda = 4: design properties at full size, the
+    device footprint of the packed tables, and a retained-cell density that
+    is a fraction of the layer pairs' state-pair slots."""
+    P = read_params(par1)
+    A, lam = 1976, 4.0
+    prot = inputs.random_protein(A, 1976)
+    w = inputs.random_codon_weights(1976)
+    plan = sd.Plan(E1, [prot], w, [lam])
+    n = 3 * A
+    cells = n * (n + 1) // 2
+    # packed tables: ~118 B per state-pair slot, 4 slots per layer pair
+    assert plan.device_bytes < cells * 4 * 130 + (1 << 30)
+    plan.run()
+    r = plan.results()[0]
+    _design_properties(P, prot, w, lam, r)
+    assert 0 < r["Z"] <= r["finite_direct"]
+    assert 0 < r["retained_cells"] < 4 * cells
+    plan.free()
+
+
+def test_bench_launch_configuration(sd, E1, par1):
+    """The configuration bench.py times (925-aa proteins in one batch,
+    predictor-presized candidate lists, fill group 8, graph replay) gives the
+    same designs as one protein per call, and each satisfies the properties."""
+    from paper_2609_32308_b300 import retention
+    P = read_params(par1)
+    seeds = [100000 + k for k in range(3)]
+    prots = [inputs.random_protein(925, s) for s in seeds]
+    ws = np.stack([inputs.random_codon_weights(s) for s in seeds])
+    plan = sd.Plan(E1, prots, ws, [4.0] * 3, predictor=retention.load(), margin=2.0)
+    plan.group = 8
+    plan.set_graph(True)
+    plan.run()
+    res = plan.results()
+    plan.free()
+    for k in range(3):
+        _design_properties(P, prots[k], ws[k], 4.0, res[k])
+    single = sd.sd_design(E1, prots[0], ws[0], 4.0)
+    for key in ("mrna", "structure", "energy", "objective_fx", "Z", "retained_cells"):
+        assert res[0][key] == single[key]
+
+
 @pytest.mark.parametrize("group", [8, 16, 32])
 def test_every_group_size_gives_the_oracle_tables(sd, E1, par1, group):
     """The fill's threads-per-layer-pair choice changes speed, never results."""
