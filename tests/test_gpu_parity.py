@@ -296,3 +296,17 @@ def test_autotune_then_graph(sd, E1):
     got = plan.results()
     assert [(r["mrna"], r["energy"]) for r in got] == [(r["mrna"], r["energy"]) for r in base]
     plan.free()
+
+
+def test_golden_oracle_designs(sd, E1):
+    """The CUDA path against designs the oracle wrote to tests/golden."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_designs.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 6
+    for A, seed, lam, mrna, st, e, ofx, Z in rows:
+        prot = inputs.random_protein(int(A), int(seed))
+        w = inputs.random_codon_weights(int(seed))
+        r = sd.sd_design(E1, prot, w, float(lam))
+        assert (r["mrna"], r["structure"], r["energy"], r["objective_fx"], r["Z"]) == \
+            (mrna, st, int(e), int(ofx), int(Z))

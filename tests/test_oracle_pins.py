@@ -199,24 +199,28 @@ def test_oracle_width1_nonzero_ml_base(par_mlbase):
         assert evaluate.energy(P, o.mrna, o.structure) == o.energy
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    with open(path) as f:
+        return [l.split() for l in f if l.strip() and not l.startswith("#")]
+
+
 def test_internal_loop_cap_30_vs_31(par1, P1):
-    """Sec. 3 / Sec. 6.1 fixture: a two-loop with 30 unpaired nucleotides is
-    inside the optimisation domain, one with 31 is not (the evaluator still
-    scores it)."""
-    outer_l, outer_r = "GGGGGGGGGGGG", "CCCCCCCCCCCC"
-    inner = "GGGGGGGGGAAAACCCCCCCCC"
-    for unp, feasible in ((30, True), (31, False)):
-        l1 = unp // 2
-        l2 = unp - l1
-        seq = outer_l + "A" * l1 + inner + "A" * l2 + outer_r
-        st = ("(" * 12 + "." * l1 + "(" * 9 + "...." + ")" * 9 + "." * l2 + ")" * 12)
+    """Sec. 3 / Sec. 6.1 fixture (tests/golden/loop_cap_30_31.txt): a two-loop
+    with 30 unpaired nucleotides is inside the optimisation domain, one with
+    31 is not (the evaluator still scores it)."""
+    rows = _golden("loop_cap_30_31.txt")
+    assert [(int(r[0]), int(r[1])) for r in rows] == [(30, 1), (31, 0)]
+    for unp, inside, seq, st in rows:
+        unp, inside = int(unp), int(inside)
         e_struct = evaluate.energy(P1, seq, st)
         assert evaluate.max_two_loop_unpaired(st) == unp
         o = oracle.run_rna(par1, seq)
         assert o.status == 0
         assert evaluate.max_two_loop_unpaired(o.structure) <= 30
         assert o.energy == zuker.mfe(P1, seq)
-        if feasible:
+        if inside:
             assert o.energy <= e_struct
         # with 31 the oracle may only do as well as structures inside the domain
         assert o.energy == evaluate.energy(P1, o.mrna, o.structure)
@@ -344,3 +348,14 @@ def test_empty_and_tiny_proteins(par1):
     bad[inputs.codon_index("AUG")] = 0.9         # max over Met's codons is not 1
     with pytest.raises(ValueError):
         oracle.run(par1, "M", bad, 1.0)
+
+
+def test_oracle_reproduces_its_golden_designs(par1):
+    """tests/golden/oracle_designs.txt was written by the oracle alone
+    (tests/golden/make_oracle_designs.py); a change to the oracle's arithmetic
+    or tie-break shows up here."""
+    for A, seed, lam, mrna, st, e, ofx, Z in _golden("oracle_designs.txt"):
+        prot = inputs.random_protein(int(A), int(seed))
+        w = inputs.random_codon_weights(int(seed))
+        o = oracle.run(par1, prot, w, float(lam))
+        assert (o.mrna, o.structure, o.energy, o.obj_fx, o.Z) == (mrna, st, int(e), int(ofx), int(Z))
