@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--cpu-sample-aa", type=int, default=80)
     ap.add_argument("--no-predictor", action="store_true",
                     help="worst-case candidate room instead of the predictor's")
+    ap.add_argument("--dense-control", action="store_true",
+                    help="also run the batch once with every finite direct interval "
+                         "retained (scalar-dense control) and report its fill time and Z")
     ap.add_argument("--once", action="store_true",
                     help="profiling case: build the batch, run it once with --group, read "
                          "the results; no timing and no JSON line")
@@ -316,6 +319,24 @@ def main():
     # no timed step overflowed a presized list (runs are deterministic)
     assert sum(r["regrows"] for r in res) == regrows
     room, room_worst = plan.candidate_room, plan.candidate_room_worst
+    dense_ctl = None
+    if args.dense_control:
+        # outside the timed region: same plan, same kernels, dense retention
+        # (presized lists overflow and are regrown to worst-case room first)
+        z_sparse = sum(r["Z"] for r in res)
+        plan.set_graph(False)
+        plan.set_dense(True)
+        plan.run(stream)
+        dres = plan.results()
+        plan.run(stream)
+        dfill = plan.phase_times()[0]
+        dres = plan.results()
+        assert [r["objective_fx"] for r in dres] == [r["objective_fx"] for r in res]
+        dense_ctl = {"fill_ms": dfill, "Z": sum(r["Z"] for r in dres), "Z_sparse": z_sparse,
+                     "sparse_fill_ms": statistics.mean(x[0] for x in phases),
+                     "note": "same optimum for every design (Thm. 1); the ratio of fill "
+                             "times is what the candidate sparsification saves"}
+        plan.set_dense(False)
     cells = sum(r["retained_cells"] for r in res)
     value = job_rate(args.batch, world, args.steps, elapsed)
     cell_rate = cells * world * args.steps / elapsed
@@ -398,6 +419,8 @@ def main():
             "batched_over_plain": value / plain_value,
             "phase_ms": {"fill": phase[0], "exterior": phase[1], "traceback": phase[2]},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
+    if dense_ctl is not None:
+        line["dense_control"] = dense_ctl
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_sample_aa, cells / args.batch)
     print(json.dumps(line), flush=True)

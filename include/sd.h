@@ -239,6 +239,15 @@ int sd_plan_create_predicted(const sd_energy *energy, sd_predictor *pred, double
                              const char *const *proteins, const double *codon_weights,
                              int weights_shared, const double *lambdas, sd_plan **out,
                              int *item_status);
+/* Scalar-dense control (a switch on the same kernels, for measuring what the
+ * sparsification saves): with enable != 0 every finite direct interval B(c,b)
+ * enters C_b instead of only those with B < P_S (Eq. candidates).  S1, S2 and
+ * every optimum are unchanged (Thm. 1); Z and the work grow, and the canonical
+ * split of a tied S2 may differ.  Presized lists that overflow are regrown as
+ * usual.  Takes effect on the next sd_plan_run (graphs need no re-capture).
+ * NULL plan: SD_EINVAL. */
+int sd_plan_set_dense(sd_plan *plan, int enable);
+
 /* Candidate-list entries reserved by a plan (all items), and the entries the
  * same items would reserve with worst-case room (every state at least five
  * layers before the list's end state).  NULL plan: 0. */

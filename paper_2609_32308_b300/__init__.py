@@ -80,6 +80,7 @@ def lib():
         L.sd_plan_retention.argtypes = [P, I, P]
         L.sd_plan_candidate_room.argtypes = [P]
         L.sd_plan_candidate_room.restype = ctypes.c_int64
+        L.sd_plan_set_dense.argtypes = [P, I]
         L.sd_plan_candidate_room_worst.argtypes = [P]
         L.sd_plan_candidate_room_worst.restype = ctypes.c_int64
         L.sd_plan_create_predicted.argtypes = [P, P, D, I, P, P, I, P, ctypes.POINTER(P), P]
@@ -104,7 +105,7 @@ def lib():
                   "sd_plan_run", "sd_plan_results", "sd_plan_item_size", "sd_plan_dump",
                   "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
-                  "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention",
+                  "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention", "sd_plan_set_dense",
                   "sd_plan_create_predicted", "sd_pred_create", "sd_pred_get_params",
                   "sd_pred_set_params", "sd_pred_features", "sd_pred_forward",
                   "sd_pred_gradients", "sd_pred_train_step"):
@@ -327,6 +328,12 @@ class Plan:
     @property
     def candidate_room(self) -> int:
         return int(lib().sd_plan_candidate_room(self.handle))
+
+    def set_dense(self, enable: bool) -> None:
+        """Scalar-dense control: retain every finite direct interval."""
+        rc = lib().sd_plan_set_dense(self.handle, int(bool(enable)))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_set_dense")
 
     @property
     def candidate_room_worst(self) -> int:

@@ -953,6 +953,18 @@ extern "C" int64_t sd_plan_candidate_room(const sd_plan *p) {
   return total;
 }
 
+extern "C" int sd_plan_set_dense(sd_plan *p, int enable) {
+  if (!p) return SD_EINVAL;
+  for (auto &d : p->hdesigns) d.dense = enable ? 1 : 0;
+  for (auto &it : p->items)
+    if (it.status == SD_OK) it.d.dense = enable ? 1 : 0;
+  if (!p->hdesigns.empty() &&
+      cudaMemcpy(p->d_designs, p->hdesigns.data(), sizeof(SdDesign) * p->hdesigns.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess)
+    return SD_ECUDA;
+  return SD_OK;
+}
+
 extern "C" int64_t sd_plan_candidate_room_worst(const sd_plan *p) {
   if (!p) return 0;
   int64_t total = 0;

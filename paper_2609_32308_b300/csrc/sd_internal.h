@@ -66,7 +66,7 @@ struct SdParams {
 struct SdDesign {
   int32_t n, N;           // nucleotides, states
   int32_t status_slot;    // index into the plan's status array
-  int32_t pad;
+  int32_t dense;          // 1: retain every finite direct interval (scalar-dense control)
   const int32_t *lstart;  // n+2
   const int32_t *layer;   // N
   const SdEdge *out;      // N * SD_MAXOUT, by label

@@ -644,16 +644,23 @@ constexpr int IL_PAIRS = 375;
 // the span kernel: a group of G threads (G = 8, 16 or 32) per layer pair
 // (i, i+g); consecutive groups take consecutive layer pairs.
 // ---------------------------------------------------------------------------
+// With G < 32 the groups of one warp take layer pairs i, i+3, i+6, ... (the
+// same position inside the codon at both ends, so the same layer types and
+// mostly the same branches); a block of 3 warps covers 3 * 32/G consecutive
+// layer pairs.
 template <int G>
 struct FillShape {
-  static constexpr int threads = 128;
+  static constexpr int threads = G == 32 ? 128 : 96;
   static constexpr int pairs = threads / G;
-  __device__ static int pair_index(int bx) { return bx * pairs + (int)threadIdx.x / G; }
+  __device__ static int pair_index(int bx) {
+    const int warp = (int)threadIdx.x >> 5, grp = ((int)threadIdx.x & 31) / G;
+    return G == 32 ? bx * pairs + warp : bx * pairs + warp + 3 * grp;
+  }
 };
 
 
 template <int G, bool COUNT>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::threads)
     k_fill_span(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp, int g,
                 int nact, int items, const int32_t *__restrict__ cpre,
                 unsigned long long *ops_out) {
@@ -1036,7 +1043,9 @@ __global__ void __launch_bounds__(128, 4)
       const int cap = D.cand_cap ? __ldg(&D.cand_cap[b]) : 0x7fffffff;
       for (int sa = wa - 1; sa >= 0; sa--) {
         const int s = sa * SD_W + sb;
-        if (Bs[s] < PSs[s]) {
+        // Eq. (candidates): strict B < P_S; the dense control keeps every
+        // finite direct interval (the sparse and dense S2 are equal, Thm. 1)
+        if (D.dense ? fin(Bs[s]) : Bs[s] < PSs[s]) {
           if (cnt < cap) {
             D.cand_c[off + cnt] = a0 + sa;
             D.cand_B[off + cnt] = Bs[s];

@@ -310,3 +310,43 @@ def test_golden_oracle_designs(sd, E1):
         r = sd.sd_design(E1, prot, w, float(lam))
         assert (r["mrna"], r["structure"], r["energy"], r["objective_fx"], r["Z"]) == \
             (mrna, st, int(e), int(ofx), int(Z))
+
+
+def test_dense_control_keeps_every_optimum(sd, E1, par1):
+    """Scalar-dense control (every finite direct interval retained): the
+    dense tables of the oracle are reproduced, the candidate sets become the
+    finite direct intervals, and the optimum is unchanged (Thm. 1)."""
+    prot = inputs.random_protein(45, 17)
+    w = inputs.random_codon_weights(17)
+    o = oracle.run(par1, prot, w, 4.0)
+    plan = sd.Plan(E1, [prot], w, [4.0])
+    plan.set_dense(True)
+    plan.run()
+    d = plan.dump(0)
+    assert np.array_equal(d["S1"], o.D1) and np.array_equal(d["S2"], o.D2)
+    assert np.array_equal(d["B"], o.B) and np.array_equal(d["V"], o.V)
+    assert np.array_equal(d["cand"].astype(bool), o.B < oracle.INF)
+    r = plan.results()[0]
+    assert r["objective_fx"] == o.obj_fx
+    assert r["Z"] == int((o.B < oracle.INF).sum()) >= o.Z
+    plan.set_dense(False)
+    plan.run()
+    assert np.array_equal(plan.dump(0)["cand"], o.cand)
+    compare_design(plan.results()[0], o, 4.0)
+    plan.free()
+
+
+def test_dense_control_full_size(sd, E1):
+    """925 aa: dense and sparse retention give the same optimum; dense keeps
+    more candidates (the work the sparsification saves)."""
+    prot = inputs.random_protein(925, 100000)
+    w = inputs.random_codon_weights(100000)
+    plan = sd.Plan(E1, [prot], w, [4.0])
+    plan.run()
+    sparse = plan.results()[0]
+    plan.set_dense(True)
+    plan.run()
+    dense = plan.results()[0]
+    plan.free()
+    assert dense["objective_fx"] == sparse["objective_fx"]
+    assert dense["Z"] > sparse["Z"]
