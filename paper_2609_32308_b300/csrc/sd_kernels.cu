@@ -1058,20 +1058,95 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
       D.cand_cnt[b] = cnt;
     }
   __syncwarp();  // the stack option reads V of this cell, written by another thread
-  // closed-interior values for the pairs two spans up, all outer types at once
+  // closed-interior values for the pairs two spans up, all outer types at once.
+  // The (layer pair, slot) cells that some outer type can close are pooled
+  // over the groups of the warp and dealt out round-robin, so that a group
+  // with one such cell does not idle while another works through four.
+  if constexpr (G == 32) {  // one group per warp: nothing to pool
 #pragma unroll 1
+    for (int s = 0; s < SD_SLOTS; s++) {
+      const int sa = s / SD_W, sb = s % SD_W;
+      const bool ok = active && sa < wa && sb < wb;
+      int tm = 0;
+      if (ok) {
+        const int im = D.in_mask[a0 + sa], om = D.out_mask[b0 + sb];
+#pragma unroll
+        for (int t = 0; t < 6; t++)
+          if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tm |= 1 << t;
+      }
+      int64_t qv[6];
+      uint32_t qk[6];
+#pragma unroll
+      for (int t = 0; t < 6; t++) {
+        qv[t] = SD_INF;
+        qk[t] = KEY_NONE;
+      }
+      if (tm) q_slot<G, COUNT>(F, D, P, T, sub, a0 + sa, b0 + sb, i, sa, j, sb, tm, qv, qk, ops, GS);
+#pragma unroll
+      for (int t = 0; t < 6; t++) {
+        if (tm) seg_lexmin<G>(qv[t], qk[t]);
+        settle(qv[t], qk[t]);
+        if (ok && sub == t % G) {
+          D.Q[(int64_t)(rcell + s) * 6 + t] = qv[t];
+          D.Qk[(int64_t)(rcell + s) * 6 + t] = qk[t];
+        }
+      }
+    }
+    if (COUNT && active && ops) atomicAdd(&ops_out[dsel], ops);
+    return;
+  }
+  if (COUNT && active && ops) atomicAdd(&ops_out[dsel], ops);
+  ops = 0;
+  constexpr int NGW = 32 / G;
+  const int grp = lane / G;
+  uint32_t tms = 0;  // 6 type bits per slot
+#pragma unroll
   for (int s = 0; s < SD_SLOTS; s++) {
     const int sa = s / SD_W, sb = s % SD_W;
     const bool ok = active && sa < wa && sb < wb;
-    const int x = a0 + sa, y = b0 + sb;
-    // outer types that can close (x, y); the same for all threads of a group
     int tm = 0;
     if (ok) {
-      const int im = D.in_mask[x], om = D.out_mask[y];
+      const int im = D.in_mask[a0 + sa], om = D.out_mask[b0 + sb];
 #pragma unroll
       for (int t = 0; t < 6; t++)
         if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tm |= 1 << t;
+      if (!tm && sub < 6) {  // no outer type can close (x, y)
+        D.Q[(int64_t)(rcell + s) * 6 + sub] = SD_INF;
+        D.Qk[(int64_t)(rcell + s) * 6 + sub] = KEY_NONE;
+      }
     }
+    tms |= (uint32_t)tm << (6 * s);
+  }
+  uint32_t words[NGW];
+  int K = 0;
+#pragma unroll
+  for (int go = 0; go < NGW; go++) {
+    words[go] = __shfl_sync(FULL, tms, go * G);
+#pragma unroll
+    for (int s = 0; s < SD_SLOTS; s++) K += ((words[go] >> (6 * s)) & 63) != 0;
+  }
+#pragma unroll 1
+  for (int r = 0; r < K; r += NGW) {
+    // this group's cell of the round: the (r + grp)-th pooled one
+    const int k = r + grp;
+    int go_k = 0, s_k = 0, tm_k = 0, c = 0;
+#pragma unroll
+    for (int go = 0; go < NGW; go++)
+#pragma unroll
+      for (int s = 0; s < SD_SLOTS; s++) {
+        const int tmv = (words[go] >> (6 * s)) & 63;
+        if (tmv) {
+          if (c == k) {
+            go_k = go;
+            s_k = s;
+            tm_k = tmv;
+          }
+          c++;
+        }
+      }
+    const int src = go_k * G;
+    const int o_dsel = __shfl_sync(FULL, dsel, src), o_i = __shfl_sync(FULL, i, src);
+    const int o_a0 = __shfl_sync(FULL, a0, src), o_b0 = __shfl_sync(FULL, b0, src);
     int64_t qv[6];
     uint32_t qk[6];
 #pragma unroll
@@ -1079,18 +1154,40 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
       qv[t] = SD_INF;
       qk[t] = KEY_NONE;
     }
-    if (tm) q_slot<G, COUNT>(F, D, P, T, sub, x, y, i, sa, j, sb, tm, qv, qk, ops, GS);
+    const SdDesign &Do = designs[o_dsel];
+    const int sa = s_k / SD_W, sb = s_k % SD_W;
+    if (tm_k) {
+      Fv Fo;
+      Fo.n = Do.n;
+      Fo.lst = Do.lstart;
+      Fo.oe = Do.out;
+      Fo.ie = Do.in;
+      Fo.on = Do.out_cnt;
+      Fo.in_ = Do.in_cnt;
+      Fo.H = Do.H;
+      Fo.Hk = Do.Hk;
+      Fo.V = Do.V;
+      Fo.lay = Do.layer;
+      Fo.fo = Do.fo;
+      Fo.fo_off = Do.fo_off;
+      Fo.fi = Do.fi;
+      Fo.fi_off = Do.fi_off;
+      q_slot<G, COUNT>(Fo, Do, P, T, sub, o_a0 + sa, o_b0 + sb, o_i, sa, o_i + g, sb, tm_k, qv,
+                       qk, ops, s_gap[(threadIdx.x >> 5) * NGW + go_k]);
+    }
+    const int o_rcell = ((g & (SD_RING - 1)) * (Do.n + 1) + o_i) * SD_SLOTS;
 #pragma unroll
     for (int t = 0; t < 6; t++) {
-      if (__any_sync(FULL, (tm >> t) & 1)) seg_lexmin<G>(qv[t], qk[t]);
+      if (__any_sync(FULL, (tm_k >> t) & 1)) seg_lexmin<G>(qv[t], qk[t]);
       settle(qv[t], qk[t]);
-      if (ok && sub == t % G) {
-        D.Q[(int64_t)(rcell + s) * 6 + t] = qv[t];
-        D.Qk[(int64_t)(rcell + s) * 6 + t] = qk[t];
+      if (tm_k && sub == t % G) {
+        Do.Q[(int64_t)(o_rcell + s_k) * 6 + t] = qv[t];
+        Do.Qk[(int64_t)(o_rcell + s_k) * 6 + t] = qk[t];
       }
     }
+    if (COUNT && tm_k && ops) atomicAdd(&ops_out[o_dsel], ops);
+    ops = 0;
   }
-  if (COUNT && active && ops) atomicAdd(&ops_out[dsel], ops);
 }
 
 // ---------------------------------------------------------------------------
