@@ -82,6 +82,25 @@ def alu_peak_tops(sm_mhz: float) -> float:
     return SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per fill launch of
+# the default workload, averaged over the 2,775 fill launches of one timed step
+# in one ncu capture (profiles/k_fill_span_traffic_bench_925aa_batch32.md).  The
+# figure belongs to the kernel source with this SHA-256; any other build reports
+# null.
+FILL_TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+
+
+def fill_traffic():
+    import hashlib
+    src = os.path.join(ROOT, "paper_2609_32308_b300", "csrc", "sd_kernels.cu")
+    try:
+        with open(src, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    return FILL_TRAFFIC["bytes_per_launch"] if digest == FILL_TRAFFIC["sha256"] else None
+
+
 class Clocks:
     """nvidia-smi sampler running during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -393,7 +412,7 @@ def main():
     achieved = ops / fill_s / 1e12
     peak = alu_peak_tops(max_mhz)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": fill_traffic(),
             "kernel": "k_fill_span",
             "work": f"{ops} algorithmic INT32 slots per fill of the batch (counted: every "
                     f"min-plus term with finite operands = 2 x (int64 adds + 1 min)), "

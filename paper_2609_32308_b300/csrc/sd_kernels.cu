@@ -660,7 +660,10 @@ struct FillShape {
 
 
 template <int G, bool COUNT>
-__global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::threads)
+#ifndef SD_FILL_MINB
+#define SD_FILL_MINB 5
+#endif
+__global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_MINB)
     k_fill_span(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp, int g,
                 int nact, int items, const int32_t *__restrict__ cpre,
                 unsigned long long *ops_out) {
@@ -847,6 +850,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
     int64_t vv[6];
     {
       const int oma = ok ? D.out_mask[a] : 0, nib = ok ? F.nin(b) : 0;
+      const int imb = ok ? D.in_mask[b] : 0;
       int64_t B = SD_INF;
       uint32_t Bk = KEY_NONE;
 #pragma unroll
@@ -856,7 +860,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, 512 / FillShape<G>::thr
         // the out-edge of a labelled with the pair's 5' nucleotide (a DFA has
         // at most one; out-edges are stored by label)
         const int l5 = c_pair5[t];
-        if (ok && g >= 5 && ((oma >> l5) & 1)) {
+        if (ok && g >= 5 && ((oma >> l5) & 1) && ((imb >> c_pair3[t]) & 1)) {
           const SdEdge e1 = F.out(a, __popc(oma & ((1 << l5) - 1)));
           const int l3 = c_pair3[t];
           for (int k2 = 0; k2 < nib; k2++) {
