@@ -87,7 +87,8 @@ def alu_peak_tops(sm_mhz: float) -> float:
 # in one ncu capture (profiles/k_fill_span_traffic_bench_925aa_batch32.md).  The
 # figure belongs to the kernel source with this SHA-256; any other build reports
 # null.
-FILL_TRAFFIC = {"sha256": None, "bytes_per_launch": None}
+FILL_TRAFFIC = {"sha256": "0a1b2da8c685b633a6b62fd84ab3d1ea7284634ae813b58223ff204a9466ffee",
+                "bytes_per_launch": 1007323187}
 
 
 def fill_traffic():
