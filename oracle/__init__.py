@@ -66,6 +66,8 @@ def _load():
         lib.orc_codon_cost_fx.restype = ctypes.c_int64
         lib.orc_hairpin_energy.argtypes = [ctypes.c_char_p, ctypes.c_char_p]
         lib.orc_hairpin_energy.restype = ctypes.c_int
+        lib.orc_twoloop_energy.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p]
+        lib.orc_twoloop_energy.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -162,3 +164,9 @@ def codon_cost_fx(lam: float, w: float) -> int:
 
 def hairpin_energy(param_path: str, seq: str) -> int:
     return int(_load().orc_hairpin_energy(param_path.encode(), seq.encode()))
+
+
+def twoloop_energy(param_path: str, left: str, right: str) -> int:
+    """Two-loop energy of the oracle's loop function: left = outer 5' nt,
+    l1 unpaired, inner 5' nt; right = inner 3' nt, l2 unpaired, outer 3' nt."""
+    return int(_load().orc_twoloop_energy(param_path.encode(), left.encode(), right.encode()))

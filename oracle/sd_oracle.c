@@ -1089,3 +1089,22 @@ int orc_hairpin_energy(const char *param_path, const char *seq) {
   free(P);
   return e;
 }
+
+/* two-loop energy exposed for fixture tests: left = nucleotides i..p (outer
+ * 5' end, l1 unpaired, inner 5' end), right = q..j (inner 3' end, l2
+ * unpaired, outer 3' end); integer dcal/mol, -999999 on bad input */
+int orc_twoloop_energy(const char *param_path, const char *left, const char *right) {
+  OParams *P = malloc(sizeof(OParams));
+  if (load_params(param_path, P)) { free(P); return -999999; }
+  int nl = (int)strlen(left), nr = (int)strlen(right), a[64], b[64];
+  if (nl < 2 || nr < 2 || nl > 64 || nr > 64) { free(P); return -999999; }
+  for (int k = 0; k < nl; k++) { a[k] = -1; for (int c = 0; c < 4; c++) if (left[k] == NT[c]) a[k] = c; }
+  for (int k = 0; k < nr; k++) { b[k] = -1; for (int c = 0; c < 4; c++) if (right[k] == NT[c]) b[k] = c; }
+  int l1 = nl - 2, l2 = nr - 2;
+  int t = pair_type(a[0], b[nr - 1]), ti = pair_type(a[nl - 1], b[0]);
+  int e = (t < 0 || ti < 0 || l1 + l2 > 30)
+              ? -999999
+              : twoloop_energy(P, t, ti, l1, l2, a[1], a[nl - 2], b[1], b[nr - 2]);
+  free(P);
+  return e;
+}

@@ -151,6 +151,40 @@ def test_oracle_hairpin_energy_matches_evaluator(par1, P1):
         assert oracle.hairpin_energy(par1, s) == evaluate.hairpin_energy(P1, s, 0, len(s) - 1)
 
 
+def _two_loop_classes():
+    """(l1, l2) of every two-loop class of the Sec. 3 model (l1 + l2 <= 30)."""
+    yield "stack", [(0, 0)]
+    yield "bulge1", [(1, 0), (0, 1)]
+    yield "bulge", [(0, l) for l in range(2, 31)] + [(l, 0) for l in range(2, 31)]
+    yield "1x1", [(1, 1)]
+    yield "1x2", [(1, 2)]
+    yield "2x1", [(2, 1)]
+    yield "2x2", [(2, 2)]
+    yield "1xn", [(1, l) for l in range(3, 30)] + [(l, 1) for l in range(3, 30)]
+    yield "2x3", [(2, 3), (3, 2)]
+    yield "generic", [(a, b) for a in range(2, 29) for b in range(2, 29)
+                      if a + b <= 30 and (a, b) not in ((2, 2), (2, 3), (3, 2))]
+
+
+@pytest.mark.parametrize("cls,shapes", list(_two_loop_classes()))
+def test_oracle_two_loop_energy_matches_evaluator(par1, P1, cls, shapes):
+    """The C oracle's two-loop function against the independent evaluator,
+    class by class, with random outer and inner pair types and loop
+    nucleotides (a swapped mismatch argument or a wrong int21 rotation in
+    any class fails here, whether or not that class is ever optimal)."""
+    rng = random.Random(sum(map(ord, cls)))
+    pairs = ["AU", "CG", "GC", "UA", "GU", "UG"]
+    for k in range(max(300, 4 * len(shapes))):
+        l1, l2 = shapes[k % len(shapes)]
+        outer, inner = rng.choice(pairs), rng.choice(pairs)
+        left = outer[0] + "".join(rng.choice(NUC) for _ in range(l1)) + inner[0]
+        right = inner[1] + "".join(rng.choice(NUC) for _ in range(l2)) + outer[1]
+        seq = left + right
+        i, p, q, j = 0, len(left) - 1, len(left), len(seq) - 1
+        exp = evaluate.interior_energy(P1, seq, i, j, p, q)
+        assert oracle.twoloop_energy(par1, left, right) == exp, (cls, left, right)
+
+
 # ----------------------------------------------------------------------
 # Zuker against exhaustive enumeration
 # ----------------------------------------------------------------------
@@ -222,7 +256,10 @@ def test_internal_loop_cap_30_vs_31(par1, P1):
         assert o.energy == zuker.mfe(P1, seq)
         if inside:
             assert o.energy <= e_struct
-        # with 31 the oracle may only do as well as structures inside the domain
+        else:
+            # the 31-unpaired structure scores strictly below the oracle's
+            # optimum: only the cap keeps it out of the domain
+            assert e_struct < o.energy
         assert o.energy == evaluate.energy(P1, o.mrna, o.structure)
 
 
