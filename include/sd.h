@@ -254,6 +254,18 @@ int sd_plan_set_dense(sd_plan *plan, int enable);
 int64_t sd_plan_candidate_room(const sd_plan *plan);
 int64_t sd_plan_candidate_room_worst(const sd_plan *plan);
 
+/* ---- measurement helper (not in the paper) ---- */
+
+/* Integer add/min throughput of the current device, the roofline
+ * denominator of the fill: a kernel with 2048 threads per SM, each running 8
+ * independent chains of x = min(x + s, t) in 32-bit (bits = 32) or 64-bit
+ * (bits = 64) integers, `iters` x 16 steps per chain, timed with CUDA events
+ * (best of three after one warm-up).  *ops_per_s counts the add and the min
+ * as one operation each.  Synchronous, legacy default stream; allocates a few
+ * MB of device memory.  Returns SD_OK, SD_EINVAL (bits not 32/64, iters <= 0,
+ * NULL out) or SD_ECUDA. */
+int sd_peak_addmin(int bits, int iters, double *ops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

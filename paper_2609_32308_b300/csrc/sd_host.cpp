@@ -142,7 +142,24 @@ extern "C" int sd_load_energy(const char *path, sd_energy **out) {
     delete E;
     return SD_EINVAL;
   }
-  cudaGetDevice(&E->device);
+  // lower bound of every two-loop energy of size (l1, l2)
+  for (int l1 = 0; l1 <= SD_MAXTWO; l1++)
+    for (int l2 = 0; l2 <= SD_MAXTWO; l2++) {
+      int lb = 0;
+      if (l1 + l2 <= SD_MAXTWO) {
+        lb = 1 << 30;
+        for (int t = 0; t < 6; t++)
+          for (int ti = 0; ti < 6; ti++)
+            for (int x = 0; x < 256; x++)
+              lb = std::min(lb, sd_twoloop_energy(P, t, ti, l1, l2, x >> 6, (x >> 4) & 3,
+                                                  (x >> 2) & 3, x & 3));
+      }
+      P.lb2[l1][l2] = lb;
+    }
+  if (cudaGetDevice(&E->device) != cudaSuccess) {
+    delete E;
+    return SD_ECUDA;
+  }
   if (cudaMalloc(&E->d, sizeof(SdParams)) != cudaSuccess) {
     delete E;
     return SD_ECUDA;
@@ -408,21 +425,13 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.fi_off = c.take<int32_t>(N + 1);
   const size_t ring = (size_t)SD_RING * (n + 1) * SD_SLOTS;
   d.H = c.take<int64_t>(ncell * SD_SLOTS);
-  d.Hk = c.take<uint8_t>(ncell * SD_SLOTS);
   d.V = c.take<int64_t>(ncell * SD_SLOTS * 6);
-  d.Vk = c.take<uint32_t>(ncell * SD_SLOTS * 6);
   d.S1 = c.take<int64_t>(ncell * SD_SLOTS);
-  d.S1k = c.take<uint32_t>(ncell * SD_SLOTS);
   d.S2 = c.take<int64_t>(ncell * SD_SLOTS);
-  d.S2k = c.take<uint32_t>(ncell * SD_SLOTS);
   d.Bv = c.take<int64_t>(ncell * SD_SLOTS);
-  d.Bk = c.take<uint8_t>(ncell * SD_SLOTS);
   d.Ihat = c.take<int64_t>(ring);
-  d.Ihk = c.take<uint32_t>(ring);
   d.IL = c.take<int64_t>(ring);
-  d.ILk = c.take<uint32_t>(ring);
   d.Q = c.take<int64_t>(ring * 6);
-  d.Qk = c.take<uint32_t>(ring * 6);
   d.W = c.take<int64_t>(ring * SD_WN);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
@@ -430,7 +439,6 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.cand_c = c.take<int32_t>(std::max<int64_t>(cap, 1));
   d.cand_B = c.take<int64_t>(std::max<int64_t>(cap, 1));
   d.Ext = c.take<int64_t>(N);
-  d.Extk = c.take<uint32_t>(N);
   d.mrna = c.take<char>(n + 1);
   d.structure = c.take<char>(n + 1);
   d.tb = c.take<int64_t>(4);
@@ -549,6 +557,7 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
   *out = nullptr;
   if (!energy || count < 0 || (count > 0 && (!proteins || !codon_weights || !lambdas)))
     return SD_EINVAL;
+  if (!sd_internal_on_energy_device(energy)) return SD_EINVAL;
   sd_plan *p = new (std::nothrow) sd_plan();
   if (!p) return SD_ENOMEM;
   p->energy = energy;
@@ -1154,6 +1163,13 @@ extern "C" int sd_internal_range_check(const sd_energy *E, int n, double qmax_su
   return range_check(E, L);
 }
 extern "C" const SdParams *sd_internal_device_params(const sd_energy *E) { return E ? E->d : nullptr; }
+// The energy set's device copy lives on the device that was current when it
+// was loaded; kernels launched with another device current would read
+// another GPU's memory.
+extern "C" int sd_internal_on_energy_device(const sd_energy *E) {
+  int dev = -1;
+  return E && cudaGetDevice(&dev) == cudaSuccess && dev == E->device;
+}
 extern "C" int32_t sd_internal_hairpin_len(const sd_energy *E, int L) {
   if (L < 3) return 0;
   return L <= 30 ? E->hairpin[L] : E->hairpin[30] + (int32_t)(E->lxc * std::log((double)L / 30.0));

@@ -60,7 +60,49 @@ struct SdParams {
   int32_t nspecial[3];          // triloops (5 nt), tetraloops (6 nt), hexaloops (8 nt)
   int32_t special_code[3][64];  // 2 bits per nucleotide, first nucleotide lowest
   int32_t special_e[3][64];
+  // lower bound of the two-loop energy over pair types and loop nucleotides,
+  // per (l1, l2) with l1 + l2 <= 30 (prunes the traceback's option search)
+  int32_t lb2[SD_MAXTWO + 1][SD_MAXTWO + 1];
 };
+
+#ifdef __CUDACC__
+#define SD_HD __host__ __device__
+#else
+#define SD_HD
+#endif
+
+// Oriented pair types AU CG GC UA GU UG: 5' / 3' nucleotides and the type of
+// the same pair read from the other side.
+SD_HD inline int sd_pair5(int t) { return t < 4 ? t : t - 2; }
+SD_HD inline int sd_pair3(int t) { return t < 4 ? 3 - t : 7 - t; }
+SD_HD inline int sd_rev(int t) { return t < 4 ? 3 - t : 9 - t; }
+
+// Two-loop energy of the Sec. 3 model (dangle-0 reading): t outer pair, ti
+// inner pair (5'->3' in the sequence), l1 / l2 unpaired on the 5' / 3' side,
+// xi1 = nucleotide after the outer 5' end, xp1 = before the inner 5' end,
+// xq1 = after the inner 3' end, xj1 = before the outer 3' end (only those that
+// exist are read).
+SD_HD inline int sd_twoloop_energy(const SdParams &P, int t, int ti, int l1, int l2, int xi1,
+                                   int xp1, int xq1, int xj1) {
+  const int s = sd_rev(ti);
+  if (l1 == 0 && l2 == 0) return P.stack[t][s];
+  if (l1 == 0 || l2 == 0) {
+    const int l = l1 + l2;
+    if (l == 1) return P.bulge[1] + P.stack[t][s];
+    return P.bulge[l] + P.au[t] + P.au[s];
+  }
+  if (l1 == 1 && l2 == 1) return P.int11[t][s][xi1 * 4 + xj1];
+  if (l1 == 1 && l2 == 2) return P.int21[t][s][xi1 * 16 + xq1 * 4 + xj1];
+  if (l1 == 2 && l2 == 1) return P.int21[s][t][xq1 * 16 + xi1 * 4 + xp1];
+  if (l1 == 2 && l2 == 2) return P.int22[t][s][xi1 * 64 + xp1 * 16 + xq1 * 4 + xj1];
+  const int d = l1 > l2 ? l1 - l2 : l2 - l1;
+  const int asym = P.ninio * d < P.maxninio ? P.ninio * d : P.maxninio;
+  if (l1 == 1 || l2 == 1)
+    return P.interior[l1 + l2] + asym + P.mm1n[t][xi1 * 4 + xj1] + P.mm1n[s][xq1 * 4 + xp1];
+  if ((l1 == 2 && l2 == 3) || (l1 == 3 && l2 == 2))
+    return P.interior[5] + P.ninio + P.mm23[t][xi1 * 4 + xj1] + P.mm23[s][xq1 * 4 + xp1];
+  return P.interior[l1 + l2] + asym + P.mmI[t][xi1 * 4 + xj1] + P.mmI[s][xq1 * 4 + xp1];
+}
 
 // One design resident on the device.
 struct SdDesign {
@@ -80,24 +122,17 @@ struct SdDesign {
   const int32_t *fo_off;  // N+1: out-edges of state v are fo[fo_off[v] .. fo_off[v+1])
   const SdFlatEdge *fi;   // E in-edges by (target, label, source)
   const int32_t *fi_off;  // N+1
-  // Every value comes with the canonical key of the option attaining it (the
-  // lexicographically smallest (value, key)); the traceback follows keys.
+  // Values only: the traceback re-derives every canonical choice from the
+  // full tables H, V, B, S1, S2 and the candidate lists.
   int64_t *H;             // ncell*SLOTS  min path cost between states
-  uint8_t *Hk;            // ncell*SLOTS  (first, last) label of the first min-cost path
   int64_t *V;             // ncell*SLOTS*6 typed closed values V_t(a,b)
-  uint32_t *Vk;           // ncell*SLOTS*6
   int64_t *S1, *S2;       // ncell*SLOTS  sparse one- / two-branch multiloop values
-  uint32_t *S1k, *S2k;    // ncell*SLOTS
   int64_t *Bv;            // ncell*SLOTS  branch interface B(a,b) = min_t V_t + beta_t
-  uint8_t *Bk;            // ncell*SLOTS  attaining pair type
   int64_t *Ihat;          // SD_RING*(n+1)*SLOTS inner pair + its loop-side mismatch
-  uint32_t *Ihk;
   int64_t *IL;            // SD_RING*(n+1)*SLOTS generic internal loops below a pair
-  uint32_t *ILk;
   int64_t *Q;             // SD_RING*(n+1)*SLOTS*6 closed-interior values per outer type
-  uint32_t *Qk;
-  // SD_RING*(n+1)*SLOTS*SD_WN inner tables of each cell (c,d): the best inner
-  // type with one loop-side term folded in, packed as value*8 + type:
+  // SD_RING*(n+1)*SLOTS*SD_WN inner tables of each cell (c,d): the minimum
+  // over the inner pair types of V plus one loop-side term:
   // [0,16) 1xn mismatch, [16,32) 2x3 mismatch, [32,48) generic mismatch, each
   // indexed (label into c)*4 + (label out of d); [48] bulge terminal penalty
   int64_t *W;
@@ -109,7 +144,6 @@ struct SdDesign {
   int32_t *cand_c;        // start states of the retained candidates
   int64_t *cand_B;        // their scalar branch costs B(c,b)
   int64_t *Ext;           // N   exterior suffix values (Sec. 5 final-column exterior)
-  uint32_t *Extk;         // N
   char *mrna, *structure; // n+1 each
   int64_t *tb;            // [0] energy, [1] path cost, [2] traceback status, [3] overflow
   int32_t *tb_stack;      // traceback work list, 4 ints per task
@@ -139,6 +173,7 @@ char sd_internal_translate(int x, int y, int z);
 int64_t sd_internal_codon_fx(double lambda, double w);
 int sd_internal_range_check(const struct sd_energy *E, int n, double qmax_sum);
 const SdParams *sd_internal_device_params(const struct sd_energy *E);
+int sd_internal_on_energy_device(const struct sd_energy *E);  // 1 iff current device == E's
 int32_t sd_internal_hairpin_len(const struct sd_energy *E, int L);
 // flat edge lists (fo, fi: E entries each; fo_off, fi_off: N+1) from the
 // per-state lists

@@ -18,11 +18,12 @@
 // i+g at span g (Sec. 5 endpoint ownership), and it scans C_b before it
 // appends, so no lock or barrier is needed inside a span.
 //
-// Canonical choices.  Next to every value the fill stores the key of the
-// option that attains it: the lexicographic minimum of (value, key), with keys
-// ordered like the canonical enumeration (the first attaining option wins a
-// tie).  Min-plus composition preserves this, so a stored key is exactly the
-// canonical choice and the traceback only follows keys.
+// Values only.  The fill stores the minimum of every cell and nothing about
+// which option attains it: a minimum does not depend on the order in which
+// the options are visited, so the fill is free to visit them in whatever
+// order suits the hardware.  The canonical choice of every traced cell (the
+// first attaining option of a fixed enumeration, Sec. 4.2 leaves ties open)
+// is re-derived afterwards by the traceback from the full tables.
 //
 // The exterior (final-column) values and the traceback run after the fill,
 // one block per design.
@@ -34,7 +35,6 @@
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t KEY_NONE = 0xffffffffu;
 
 __constant__ int c_pair5[6] = {0, 1, 2, 3, 2, 3};
 __constant__ int c_pair3[6] = {3, 2, 1, 0, 3, 2};
@@ -47,47 +47,13 @@ __device__ __forceinline__ int64_t diag_off(int64_t n, int64_t g) {
   return (g - 1) * (n + 1) - (g - 1) * g / 2;
 }
 
-// lexicographic (value, key) minimum
-__device__ __forceinline__ void upd(int64_t &bv, uint32_t &bk, int64_t v, uint32_t k) {
-  if (v < bv || (v == bv && k < bk)) {
-    bv = v;
-    bk = k;
-  }
-}
-__device__ __forceinline__ void warp_lexmin(int64_t &v, uint32_t &k) {
+__device__ __forceinline__ void upd(int64_t &bv, int64_t v) { bv = v < bv ? v : bv; }
+__device__ __forceinline__ void warp_min(int64_t &v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const int64_t v2 = __shfl_xor_sync(FULL, v, o);
-    const uint32_t k2 = __shfl_xor_sync(FULL, k, o);
-    upd(v, k, v2, k2);
-  }
+  for (int o = 16; o > 0; o >>= 1) upd(v, __shfl_xor_sync(FULL, v, o));
 }
-__device__ __forceinline__ void settle(int64_t &v, uint32_t &k) {
-  if (!fin(v)) {
-    v = SD_INF;
-    k = KEY_NONE;
-  }
-}
-
-// Key layout of closed-interior (Q) and typed closed (V) values:
-//   [31:27] index of the last edge into b (V only)
-//   [26:25] class: 0 hairpin, 1 two-loop, 2 multiloop
-//   two-loop: [24:20] l1+l2, [19:15] l1, [14:13] slot of c, [12:11] slot of d,
-//             [10:8] inner type, [7:6] fL, [5:4] lL, [3:2] fR, [1:0] lR
-//             (first / last nucleotide of the left and right unpaired sides;
-//             for a 1-nt side both are its nucleotide, for none both are 0)
-//   hairpin : special lengths: the loop labels, first label most significant;
-//             otherwise first*4 + last loop nucleotide
-// This order is the canonical enumeration order of the options.
-__device__ __forceinline__ uint32_t tl_key(int l1, int l2, int cs, int ds, int ti, int fL, int lL,
-                                           int fR, int lR) {
-  return (1u << 25) | ((uint32_t)(l1 + l2) << 20) | ((uint32_t)l1 << 15) | ((uint32_t)cs << 13) |
-         ((uint32_t)ds << 11) | ((uint32_t)ti << 8) | ((uint32_t)fL << 6) | ((uint32_t)lL << 4) |
-         ((uint32_t)fR << 2) | (uint32_t)lR;
-}
-constexpr uint32_t KEY_ML = 2u << 25;
-constexpr uint32_t KEY_QMASK = (1u << 27) - 1;
-constexpr uint32_t KEY_SPLIT = 1u << 30;  // S2 candidate split / exterior branch
+// every value >= 2^59 is +infinity; store it as SD_INF
+__device__ __forceinline__ int64_t settle(int64_t v) { return fin(v) ? v : SD_INF; }
 
 struct Lat {
   const SdDesign &D;
@@ -134,30 +100,6 @@ struct Lat {
 // loop energies (integer dcal/mol), Sec. 3 model
 // ---------------------------------------------------------------------------
 
-// two-loop energy; t outer pair, ti inner pair, xi1 = nt i+1, xp1 = nt p-1,
-// xq1 = nt q+1, xj1 = nt j-1 (only those that exist are read)
-__device__ int twoloop_e(const SdParams &P, int t, int ti, int l1, int l2, int xi1, int xp1,
-                         int xq1, int xj1) {
-  const int s = c_rev[ti];
-  if (l1 == 0 && l2 == 0) return P.stack[t][s];
-  if (l1 == 0 || l2 == 0) {
-    const int l = l1 + l2;
-    if (l == 1) return P.bulge[1] + P.stack[t][s];
-    return P.bulge[l] + P.au[t] + P.au[s];
-  }
-  if (l1 == 1 && l2 == 1) return P.int11[t][s][xi1 * 4 + xj1];
-  if (l1 == 1 && l2 == 2) return P.int21[t][s][xi1 * 16 + xq1 * 4 + xj1];
-  if (l1 == 2 && l2 == 1) return P.int21[s][t][xq1 * 16 + xi1 * 4 + xp1];
-  if (l1 == 2 && l2 == 2) return P.int22[t][s][xi1 * 64 + xp1 * 16 + xq1 * 4 + xj1];
-  const int d = l1 > l2 ? l1 - l2 : l2 - l1;
-  const int asym = min(P.maxninio, P.ninio * d);
-  if (l1 == 1 || l2 == 1)
-    return P.interior[l1 + l2] + asym + P.mm1n[t][xi1 * 4 + xj1] + P.mm1n[s][xq1 * 4 + xp1];
-  if ((l1 == 2 && l2 == 3) || (l1 == 3 && l2 == 2))
-    return P.interior[5] + P.ninio + P.mm23[t][xi1 * 4 + xj1] + P.mm23[s][xq1 * 4 + xp1];
-  return P.interior[l1 + l2] + asym + P.mmI[t][xi1 * 4 + xj1] + P.mmI[s][xq1 * 4 + xp1];
-}
-
 __device__ __forceinline__ int hairpin_generic_e(const SdParams &P, const int32_t *hp_len, int t,
                                                  int L, int f, int l) {
   if (L == 3) return __ldg(&hp_len[3]) + P.au[t];
@@ -197,13 +139,9 @@ struct SmallTables {
 };
 
 template <int G>
-__device__ __forceinline__ void seg_lexmin(int64_t &v, uint32_t &k) {
+__device__ __forceinline__ void seg_min(int64_t &v) {
 #pragma unroll
-  for (int o = G / 2; o > 0; o >>= 1) {
-    const int64_t v2 = __shfl_xor_sync(FULL, v, o);
-    const uint32_t k2 = __shfl_xor_sync(FULL, k, o);
-    upd(v, k, v2, k2);
-  }
+  for (int o = G / 2; o > 0; o >>= 1) upd(v, __shfl_xor_sync(FULL, v, o));
 }
 
 // Design view for the fill: hot pointers in registers, 32-bit index math
@@ -216,7 +154,6 @@ struct Fv {
   const uint8_t *__restrict__ on;
   const uint8_t *__restrict__ in_;
   const int64_t *H;
-  const uint8_t *Hk;
   const int64_t *V;
   const int32_t *__restrict__ lay;
   const SdFlatEdge *__restrict__ fo;
@@ -257,58 +194,43 @@ struct Fv {
 
 // Gap values of the two ends of a layer pair, staged in shared memory per
 // group: hl[l][c*2 + s] = H(slot s of layer i -> slot c of layer i+l),
-// hr[l][c*2 + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW,
-// with the (first, last) label keys; the two-loop options read them many times.
+// hr[l][c*2 + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW;
+// the two-loop options read them many times.
 constexpr int SD_GAPW = SD_MAXTWO + 1;
 struct GapStage {
   int64_t hl[SD_GAPW][4], hr[SD_GAPW][4];
-  uint8_t hlk[SD_GAPW][4], hrk[SD_GAPW][4];
 };
 
-// lexicographic minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
-__device__ __forceinline__ void best_inner(const int64_t (&vv)[6], const int32_t (*tab)[16], int idx,
-                                           int64_t &bv, int &bt) {
-  bv = SD_INF;
-  bt = 7;
+// minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
+__device__ __forceinline__ int64_t best_inner(const int64_t (&vv)[6], const int32_t (*tab)[16],
+                                              int idx) {
+  int64_t bv = SD_INF;
 #pragma unroll
   for (int ti = 0; ti < 6; ti++)
-    if (fin(vv[ti])) {
-      const int64_t v = vv[ti] + fx(tab[c_rev[ti]][idx]);
-      if (v < bv) {
-        bv = v;
-        bt = ti;
-      }
-    }
+    if (fin(vv[ti])) upd(bv, vv[ti] + fx(tab[c_rev[ti]][idx]));
+  return bv;
 }
 
-// lexicographic minimum over the inner pair types of vv[ti] + AU(rev ti)
-__device__ __forceinline__ void best_au(const int64_t (&vv)[6], const int32_t *au, int64_t &bv,
-                                        int &bt) {
-  bv = SD_INF;
-  bt = 7;
+// minimum over the inner pair types of vv[ti] + AU(rev ti)
+__device__ __forceinline__ int64_t best_au(const int64_t (&vv)[6], const int32_t *au) {
+  int64_t bv = SD_INF;
 #pragma unroll
   for (int ti = 0; ti < 6; ti++)
-    if (fin(vv[ti])) {
-      const int64_t v = vv[ti] + fx(au[c_rev[ti]]);
-      if (v < bv) {
-        bv = v;
-        bt = ti;
-      }
-    }
+    if (fin(vv[ti])) upd(bv, vv[ti] + fx(au[c_rev[ti]]));
+  return bv;
 }
 
-// All outer pair types of one closed-interior cell at once: (qv[t], qk[t]) is
-// the running (value, key) minimum of Q_t for every t in the type mask tm
-// (the same for every thread of a group).  tab(t) is the outer-type part of
-// the loop energy; the rest of the term is shared by the types.
+// All outer pair types of one closed-interior cell at once: qv[t] is the
+// running minimum of Q_t for every t in the type mask tm (the same for every
+// thread of a group).  tab(t) is the outer-type part of the loop energy; the
+// rest of the term is shared by the types.
 template <bool COUNT, class Tab>
-__device__ __forceinline__ void upd6(int64_t (&qv)[6], uint32_t (&qk)[6], int tm, int64_t base,
-                                     uint32_t key, int nadd, unsigned long long &ops,
-                                     const Tab &tab) {
+__device__ __forceinline__ void upd6(int64_t (&qv)[6], int tm, int64_t base, int nadd,
+                                     unsigned long long &ops, const Tab &tab) {
 #pragma unroll
   for (int t = 0; t < 6; t++)
     if ((tm >> t) & 1) {
-      upd(qv[t], qk[t], base + fx(tab(t)), key);
+      upd(qv[t], base + fx(tab(t)));
       if (COUNT) ops += 2 * (nadd + 1);
     }
 }
@@ -336,15 +258,14 @@ template <int G, bool COUNT>
 __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdParams &P,
                                        const SmallTables &T, int sub, int x, int y, int lx,
                                        int sx, int ly, int sy, int tm, int64_t (&qv)[6],
-                                       uint32_t (&qk)[6], unsigned long long &ops,
-                                       const GapStage &GS) {
+                                       unsigned long long &ops, const GapStage &GS) {
   const int g = ly - lx;
   const int nox = F.nout(x), niy = F.nin(y);
   const int lx1s = F.ls(lx + 1), ly1s = F.ls(ly - 1);
   // ---- hairpin (loop length L = g) ----
   if (g == 3 || g == 4 || g == 6) {
     if (sub == 0) {
-      // every interior path, lexicographic label order; special loops by sequence
+      // every interior path; special loops by sequence
       int st[8], kk[8];
       int64_t cst[8];
       uint32_t labs[8];
@@ -359,7 +280,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
 #pragma unroll
           for (int t = 0; t < 6; t++)
             if ((tm >> t) & 1) {
-              upd(qv[t], qk[t], fx(hairpin_seq_e(P, D.hp_len, t, lb, g)) + cst[g], lb);
+              upd(qv[t], fx(hairpin_seq_e(P, D.hp_len, t, lb, g)) + cst[g]);
               TERM(g);
             }
           depth--;
@@ -389,8 +310,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int64_t h = F.Hh(lx + 1, e1.other - lx1s, ly - 1, e2.other - ly1s);
       if (!fin(h)) continue;
       const int idx = e1.label * 4 + e2.label;
-      upd6<COUNT>(qv, qk, tm, e1.cost + e2.cost + h + he, (uint32_t)idx, 3, ops,
-                  [&](int t) { return T.mmH[t][idx]; });
+      upd6<COUNT>(qv, tm, e1.cost + e2.cost + h + he, 3, ops, [&](int t) { return T.mmH[t][idx]; });
     }
   }
   if (g < 5) return;
@@ -406,24 +326,18 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int lv = F.layer(v), sv = v - F.ls(lv);
       const int l = right ? ly - lv : lv - lx;
       int64_t h = 0;
-      int hk = 0;
       if (l > 0) {
         h = right ? GS.hr[l][sv * 2 + sy] : GS.hl[l][sv * 2 + sx];
         if (!fin(h)) continue;
-        hk = right ? GS.hrk[l][sv * 2 + sy] : GS.hlk[l][sv * 2 + sx];
       } else if (sv != sy) {
         continue;
       }
-      const int cs = right ? sx : sv, ds = right ? sv : sy;
-      const uint32_t kb = right ? tl_key(0, l, cs, ds, 0, 0, 0, hk >> 2, hk & 3)
-                                : tl_key(l, 0, cs, ds, 0, hk >> 2, hk & 3, 0, 0);
       if (l >= 2) {
         // bulge: bulge[l] + AU(t) + AU(inner); best inner type from the inner table
         const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
-        const int64_t pk = D.W[(int64_t)rc * SD_WN + 48];
-        if (!fin(pk)) continue;
-        upd6<COUNT>(qv, qk, tm, (pk >> 3) + h + fx(T.bulge[l]), kb | ((uint32_t)(pk & 7) << 8), 2,
-                    ops, [&](int t) { return T.au[t]; });
+        const int64_t w = D.W[(int64_t)rc * SD_WN + 48];
+        if (!fin(w)) continue;
+        upd6<COUNT>(qv, tm, w + h + fx(T.bulge[l]), 2, ops, [&](int t) { return T.au[t]; });
       } else {
         int64_t vv[6];
         F.v6(right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy), vv);
@@ -432,8 +346,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int ti = 0; ti < 6; ti++) {
           if (!fin(vv[ti])) continue;
           const int s = c_rev[ti];
-          upd6<COUNT>(qv, qk, tm, vv[ti] + e1, kb | ((uint32_t)ti << 8), 2, ops,
-                      [&](int t) { return T.stack[t][s]; });
+          upd6<COUNT>(qv, tm, vv[ti] + e1, 2, ops, [&](int t) { return T.stack[t][s]; });
         }
       }
     }
@@ -455,17 +368,16 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int a = 0; a < nox; a++) {
           const SdEdge ec = F.out(x, a);
           const int p = ec.label, cs = ec.other - lx1s;
-          const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR];
-          if (!fin(pk)) continue;
-          const int64_t base = (pk >> 3) + ec.cost + r1.cost + e0;
-          const int wt = (int)(pk & 7);
+          const int64_t w = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR];
+          if (!fin(w)) continue;
+          const int64_t base = w + ec.cost + r1.cost + e0;
           for (int b2 = 0; b2 < niy; b2++) {
             const SdEdge r2 = F.in(y, b2);
             const int64_t h = F.Hh(ld + 1, u - lus, ly - 1, r2.other - ly1s);
             if (!fin(h)) continue;
             const int lR = r2.label;
-            upd6<COUNT>(qv, qk, tm, base + h + r2.cost, tl_key(1, l2, cs, ds, wt, p, p, fR, lR), 5,
-                        ops, [&](int t) { return T.mm1n[t][p * 4 + lR]; });
+            upd6<COUNT>(qv, tm, base + h + r2.cost, 5, ops,
+                        [&](int t) { return T.mm1n[t][p * 4 + lR]; });
           }
         }
       } else if (l2 == 1) {
@@ -480,7 +392,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
           for (int ti = 0; ti < 6; ti++) {
             if (!fin(vv[ti])) continue;
             const int s = c_rev[ti];
-            upd6<COUNT>(qv, qk, tm, vv[ti] + base, tl_key(1, 1, cs, ds, ti, p, p, fR, fR), 3, ops,
+            upd6<COUNT>(qv, tm, vv[ti] + base, 3, ops,
                         [&](int t) { return P.int11[t][s][p * 4 + fR]; });
           }
         }
@@ -499,8 +411,8 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
             for (int ti = 0; ti < 6; ti++) {
               if (!fin(vv[ti])) continue;
               const int s = c_rev[ti];
-              upd6<COUNT>(qv, qk, tm, vv[ti] + base, tl_key(1, 2, cs, ds, ti, p, p, fR, lR), 4,
-                          ops, [&](int t) { return P.int21[t][s][p * 16 + fR * 4 + lR]; });
+              upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
+                          [&](int t) { return P.int21[t][s][p * 16 + fR * 4 + lR]; });
             }
           }
         }
@@ -524,17 +436,16 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int b = 0; b < niy; b++) {
           const SdEdge er = F.in(y, b);
           const int r = er.label, ds = er.other - ly1s;
-          const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r];
-          if (!fin(pk)) continue;
-          const int64_t base = (pk >> 3) + er.cost + p2.cost + e0;
-          const int wt = (int)(pk & 7);
+          const int64_t wv = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r];
+          if (!fin(wv)) continue;
+          const int64_t base = wv + er.cost + p2.cost + e0;
           for (int a = 0; a < nox; a++) {
             const SdEdge p1 = F.out(x, a);
             const int64_t h = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lws);
             if (!fin(h)) continue;
             const int fL = p1.label;
-            upd6<COUNT>(qv, qk, tm, base + h + p1.cost, tl_key(l1, 1, cs, ds, wt, fL, lL, r, r), 5,
-                        ops, [&](int t) { return T.mm1n[t][fL * 4 + r]; });
+            upd6<COUNT>(qv, tm, base + h + p1.cost, 5, ops,
+                        [&](int t) { return T.mm1n[t][fL * 4 + r]; });
           }
         }
       } else {  // l1 == 2: explicit 2-edge left side
@@ -552,8 +463,8 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
             for (int ti = 0; ti < 6; ti++) {
               if (!fin(vv[ti])) continue;
               const int s = c_rev[ti];
-              upd6<COUNT>(qv, qk, tm, vv[ti] + base, tl_key(2, 1, cs, ds, ti, fL, lL, r, r), 4,
-                          ops, [&](int t) { return P.int21[s][t][r * 16 + fL * 4 + lL]; });
+              upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
+                          [&](int t) { return P.int21[s][t][r * 16 + fL * 4 + lL]; });
             }
           }
         }
@@ -576,16 +487,13 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int w = p2.wl >> 2, lL = p2.wl & 3, u = r1.wl >> 2, fR = r1.wl & 3;
       int64_t vv[6];
       int64_t wv = SD_INF;
-      int wt = 7;
       if (cls == 0) {
         F.v6(F.cs(lc, cs, ld, ds), vv);
         if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
           continue;
       } else {
-        const int64_t pk = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR];
-        if (!fin(pk)) continue;
-        wv = pk >> 3;
-        wt = (int)(pk & 7);
+        wv = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR];
+        if (!fin(wv)) continue;
       }
       for (int a = 0; a < nox; a++) {
         const SdEdge p1 = F.out(x, a);
@@ -598,8 +506,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
           const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
           const int fL = p1.label, lR = r2.label;
           if (cls) {
-            upd6<COUNT>(qv, qk, tm, wv + hc + fx(T.interior[5] + T.ninio),
-                        tl_key(l1, l2, cs, ds, wt, fL, lL, fR, lR), 8, ops,
+            upd6<COUNT>(qv, tm, wv + hc + fx(T.interior[5] + T.ninio), 8, ops,
                         [&](int t) { return T.mm23[t][fL * 4 + lR]; });
           } else {
             const int idx = fL * 64 + lL * 16 + fR * 4 + lR;
@@ -607,8 +514,8 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
             for (int ti = 0; ti < 6; ti++) {
               if (!fin(vv[ti])) continue;
               const int s = c_rev[ti];
-              upd6<COUNT>(qv, qk, tm, vv[ti] + hc, tl_key(2, 2, cs, ds, ti, fL, lL, fR, lR), 8,
-                          ops, [&](int t) { return P.int22[t][s][idx]; });
+              upd6<COUNT>(qv, tm, vv[ti] + hc, 8, ops,
+                          [&](int t) { return P.int22[t][s][idx]; });
             }
           }
         }
@@ -624,15 +531,13 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int64_t il = D.IL[r];
       if (!fin(il)) continue;
       const int idx = e1.label * 4 + e2.label;
-      upd6<COUNT>(qv, qk, tm, il + e1.cost + e2.cost,
-                  (1u << 25) | D.ILk[r] | ((uint32_t)e1.label << 6) | (uint32_t)e2.label, 3, ops,
-                  [&](int t) { return T.mmI[t][idx]; });
+      upd6<COUNT>(qv, tm, il + e1.cost + e2.cost, 3, ops, [&](int t) { return T.mmI[t][idx]; });
     }
   // ---- multiloop closed by the pair ----
   if (g >= 10 && sub == G - 1) {
     const int64_t s2 = D.S2[F.cs(lx, sx, ly, sy)];
     if (fin(s2))
-      upd6<COUNT>(qv, qk, tm, s2 + fx(T.mlclosing + T.mlintern), KEY_ML, 1, ops,
+      upd6<COUNT>(qv, tm, s2 + fx(T.mlclosing + T.mlintern), 1, ops,
                   [&](int t) { return T.au[t]; });
   }
 }
@@ -659,10 +564,10 @@ struct FillShape {
 };
 
 
-template <int G, bool COUNT>
 #ifndef SD_FILL_MINB
 #define SD_FILL_MINB 5
 #endif
+template <int G, bool COUNT>
 __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_MINB)
     k_fill_span(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp, int g,
                 int nact, int items, const int32_t *__restrict__ cpre,
@@ -724,7 +629,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   F.on = D.out_cnt;
   F.in_ = D.in_cnt;
   F.H = D.H;
-  F.Hk = D.Hk;
   F.V = D.V;
   F.lay = D.layer;
   F.fo = D.fo;
@@ -749,31 +653,12 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     for (int q = sub; q < SD_GAPW * 4; q += G) {
       const int l = q >> 2, c = (q >> 1) & 1, sn = q & 1;
       int64_t vl = SD_INF, vr = SD_INF;
-      uint8_t kl = 0, kr = 0;
       if (active && l <= lmax) {
-        if (sn < wa && c < F.w(i + l)) {
-          if (l == 0) {
-            vl = c == sn ? 0 : SD_INF;
-          } else {
-            const int h = F.cs(i, sn, i + l, c);
-            vl = F.H[h];
-            kl = F.Hk[h];
-          }
-        }
-        if (sn < wb && c < F.w(j - l)) {
-          if (l == 0) {
-            vr = c == sn ? 0 : SD_INF;
-          } else {
-            const int h = F.cs(j - l, c, j, sn);
-            vr = F.H[h];
-            kr = F.Hk[h];
-          }
-        }
+        if (sn < wa && c < F.w(i + l)) vl = l == 0 ? (c == sn ? 0 : SD_INF) : F.H[F.cs(i, sn, i + l, c)];
+        if (sn < wb && c < F.w(j - l)) vr = l == 0 ? (c == sn ? 0 : SD_INF) : F.H[F.cs(j - l, c, j, sn)];
       }
       GS.hl[l][c * 2 + sn] = vl;
       GS.hr[l][c * 2 + sn] = vr;
-      GS.hlk[l][c * 2 + sn] = kl;
-      GS.hrk[l][c * 2 + sn] = kr;
     }
     __syncwarp();
   }
@@ -792,59 +677,36 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     // gap cell (every thread of the group; at most a few in-edges)
     if (ok) {
       int64_t hv = SD_INF;
-      uint32_t hk = KEY_NONE;
       const int nib = F.nin(b);
 #pragma unroll
       for (int k = 0; k < SD_MAXIN; k++) {
         if (k >= nib) break;
         const SdEdge e = F.in(b, k);
-        int64_t hp;
-        int f;
-        if (g == 1) {
-          hp = e.other == a ? 0 : SD_INF;
-          f = e.label;
-        } else {
-          const int q = F.cs(i, sa, j - 1, e.other - js);
-          hp = F.H[q];
-          f = F.Hk[q] >> 2;
-        }
+        const int64_t hp = g == 1 ? (e.other == a ? 0 : SD_INF) : F.H[F.cs(i, sa, j - 1, e.other - js)];
         if (!fin(hp)) continue;
-        upd(hv, hk, hp + e.cost, (uint32_t)(f * 4 + e.label));
+        upd(hv, hp + e.cost);
         TERM(1);
       }
-      settle(hv, hk);
-      if (sub == 0) {
-        D.H[cell + s] = hv;
-        D.Hk[cell + s] = (uint8_t)(hk & 15);
-      }
+      if (sub == 0) D.H[cell + s] = settle(hv);
     }
-    // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side
-    // mismatch; key fields: slot of c, slot of d, inner type, lL, fR
+    // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side mismatch
     {
       int64_t iv = SD_INF;
-      uint32_t ik = KEY_NONE;
       if (ok && g >= 7) {
         const int no = F.nout(a), ni = F.nin(b);
         for (int q = sub; q < no * ni; q += G) {
           const int k2 = q % ni, k1 = q / ni;
           const SdEdge e1 = F.out(a, k1), e2 = F.in(b, k2);
           const int cs = e1.other - i1s, ds = e2.other - js;
-          const int64_t pk =
+          const int64_t w =
               D.W[(int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label];
-          if (!fin(pk)) continue;
-          const uint32_t key = ((uint32_t)cs << 13) | ((uint32_t)ds << 11) |
-                               ((uint32_t)(pk & 7) << 8) | ((uint32_t)e1.label << 4) |
-                               ((uint32_t)e2.label << 2);
-          upd(iv, ik, (pk >> 3) + e1.cost + e2.cost, key);
+          if (!fin(w)) continue;
+          upd(iv, w + e1.cost + e2.cost);
           TERM(3);
         }
       }
-      seg_lexmin<G>(iv, ik);
-      settle(iv, ik);
-      if (ok && sub == 0) {
-        D.Ihat[rcell + s] = iv;
-        D.Ihk[rcell + s] = ik;
-      }
+      seg_min<G>(iv);
+      if (ok && sub == 0) D.Ihat[rcell + s] = settle(iv);
     }
     // typed closed values (every thread of the group) and Eq. (branch)
     int64_t vv[6];
@@ -852,11 +714,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       const int oma = ok ? D.out_mask[a] : 0, nib = ok ? F.nin(b) : 0;
       const int imb = ok ? D.in_mask[b] : 0;
       int64_t B = SD_INF;
-      uint32_t Bk = KEY_NONE;
 #pragma unroll
       for (int t = 0; t < 6; t++) {
         int64_t v = SD_INF;
-        uint32_t vk = KEY_NONE;
         // the out-edge of a labelled with the pair's 5' nucleotide (a DFA has
         // at most one; out-edges are stored by label)
         const int l5 = c_pair5[t];
@@ -866,29 +726,22 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           for (int k2 = 0; k2 < nib; k2++) {
             const SdEdge e2 = F.in(b, k2);
             if (e2.label != l3) continue;
-            const int r = F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t;
-            const int64_t q = D.Q[r];
-            if (!fin(q)) continue;
-            upd(v, vk, q + e1.cost + e2.cost, ((uint32_t)k2 << 27) | D.Qk[r]);
+            const int64_t qv = D.Q[F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t];
+            if (!fin(qv)) continue;
+            upd(v, qv + e1.cost + e2.cost);
             TERM(2);
           }
         }
-        settle(v, vk);
+        v = settle(v);
         vv[t] = v;
-        if (ok && sub == t % G) {
-          D.V[(int64_t)(cell + s) * 6 + t] = v;
-          D.Vk[(int64_t)(cell + s) * 6 + t] = vk;
-        }
+        if (ok && sub == t % G) D.V[(int64_t)(cell + s) * 6 + t] = v;
         if (fin(v)) {
-          upd(B, Bk, v + fx(T.mlintern + T.au[t]), (uint32_t)t);
+          upd(B, v + fx(T.mlintern + T.au[t]));
           TERM(1);
         }
       }
-      settle(B, Bk);
-      if (ok && sub == 0) {
-        D.Bv[cell + s] = B;
-        D.Bk[cell + s] = (uint8_t)(Bk & 7);
-      }
+      B = settle(B);
+      if (ok && sub == 0) D.Bv[cell + s] = B;
       Bs[s] = B;
     }
     // inner tables of this cell for the two-loops that will enclose it
@@ -897,17 +750,16 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       int64_t *Wc = D.W + (int64_t)(rcell + s) * SD_WN;
       for (int q = sub; q < SD_WN; q += G) {
         int64_t bv = SD_INF;
-        int bt = 7;
         if (g >= 5) {
           if (q < 48) {
             const int tab = q >> 4, li = (q >> 2) & 3, lo = q & 3;
             if (((im >> li) & 1) && ((om >> lo) & 1))
-              best_inner(vv, tab == 0 ? T.mm1n : tab == 1 ? T.mm23 : T.mmI, lo * 4 + li, bv, bt);
+              bv = best_inner(vv, tab == 0 ? T.mm1n : tab == 1 ? T.mm23 : T.mmI, lo * 4 + li);
           } else {
-            best_au(vv, T.au, bv, bt);
+            bv = best_au(vv, T.au);
           }
         }
-        Wc[q] = fin(bv) ? bv * 8 + bt : SD_INF;
+        Wc[q] = settle(bv);
       }
     }
   }
@@ -916,12 +768,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   // gap values of both ends come from the staged vectors
   if (g >= 9) {
     int64_t lv[SD_SLOTS];
-    uint32_t lk[SD_SLOTS];
 #pragma unroll
-    for (int s = 0; s < SD_SLOTS; s++) {
-      lv[s] = SD_INF;
-      lk[s] = KEY_NONE;
-    }
+    for (int s = 0; s < SD_SLOTS; s++) lv[s] = SD_INF;
     if (active)
       for (int q = sub; q < IL_PAIRS; q += G) {
         const int pr = s_il[q];
@@ -929,7 +777,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         const int lc = i + l1p, ld = j - l2p;
         if (ld - lc < 7) continue;
         const int64_t e = fx(s_ile[q]);
-        const uint32_t kl = ((uint32_t)(l1p + l2p + 4) << 20) | ((uint32_t)(l1p + 2) << 15);
         const int rb = (((ld - lc) & (SD_RING - 1)) * (n + 1) + lc) * SD_SLOTS;
         // slots beyond a layer's width have +inf staged gap values
 #pragma unroll
@@ -940,16 +787,14 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           for (int ds = 0; ds < SD_W; ds++) {
             const int64_t hr0 = GS.hr[l2p][ds * 2], hr1 = GS.hr[l2p][ds * 2 + 1];
             if (!fin(hr0) && !fin(hr1)) continue;
-            const int r = rb + cs * SD_W + ds;
-            const int64_t v = D.Ihat[r];
+            const int64_t v = D.Ihat[rb + cs * SD_W + ds];
             if (!fin(v)) continue;
-            const uint32_t key = kl | D.Ihk[r];
             const int64_t ve = v + e;
 #pragma unroll
             for (int s = 0; s < SD_SLOTS; s++) {
               const int64_t h1 = (s >> 1) ? hl1 : hl0, h2 = (s & 1) ? hr1 : hr0;
               if (fin(h1) && fin(h2)) {
-                upd(lv[s], lk[s], h1 + ve + h2, key);
+                upd(lv[s], h1 + ve + h2);
                 TERM(3);
               }
             }
@@ -958,20 +803,13 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       }
 #pragma unroll
     for (int s = 0; s < SD_SLOTS; s++) {
-      seg_lexmin<G>(lv[s], lk[s]);
-      settle(lv[s], lk[s]);
-      if (active && (s >> 1) < wa && (s & 1) < wb && sub == s % G) {
-        D.IL[rcell + s] = lv[s];
-        D.ILk[rcell + s] = lk[s];
-      }
+      seg_min<G>(lv[s]);
+      if (active && (s >> 1) < wa && (s & 1) < wb && sub == s % G) D.IL[rcell + s] = settle(lv[s]);
     }
   } else if (active && sub == 0) {
 #pragma unroll
     for (int s = 0; s < SD_SLOTS; s++)
-      if ((s >> 1) < wa && (s & 1) < wb) {
-        D.IL[rcell + s] = SD_INF;
-        D.ILk[rcell + s] = KEY_NONE;
-      }
+      if ((s >> 1) < wa && (s & 1) < wb) D.IL[rcell + s] = SD_INF;
   }
   // Eq. (sparse2) for every slot: edge extensions, then splits at retained
   // candidates (the group splits the candidate list)
@@ -981,14 +819,13 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const bool ok = active && sa < wa && sb < wb;
     const int a = a0 + sa, b = b0 + sb;
     int64_t s2 = SD_INF;
-    uint32_t s2k = KEY_NONE;
     if (ok) {
       if (g >= 2 && sub == 0)
         for (int k = 0; k < F.nin(b); k++) {
           const SdEdge e = F.in(b, k);
           const int64_t v = D.S2[F.cs(i, sa, j - 1, e.other - js)];
           if (!fin(v)) continue;
-          upd(s2, s2k, v + e.cost + mlb, (uint32_t)k);
+          upd(s2, v + e.cost + mlb);
           TERM(2);
         }
       const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
@@ -999,41 +836,36 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         if (lc <= i) break;  // entries are in decreasing layer order
         const int64_t v = D.S1[F.cs(i, sa, lc, c - F.ls(lc))];
         if (!fin(v)) continue;
-        upd(s2, s2k, v + D.cand_B[off + k], KEY_SPLIT | (uint32_t)c);
+        upd(s2, v + D.cand_B[off + k]);
         TERM(1);
       }
     }
-    seg_lexmin<G>(s2, s2k);
-    settle(s2, s2k);
+    seg_min<G>(s2);
+    s2 = settle(s2);
     if (ok && sub == 0) {
       D.S2[cell + s] = s2;
-      D.S2k[cell + s] = s2k;
-      // P_S (Eq. partitionable with S) and S1 = min(B, P_S); key classes:
-      // 0 direct branch, 1 left peel, 2 right peel, 3 two-branch value
+      // P_S (Eq. partitionable with S) and S1 = min(B, P_S)
       int64_t ps = s2;
-      uint32_t psk = fin(s2) ? (3u << 4) : KEY_NONE;
       if (g >= 2) {
         for (int k = 0; k < F.nout(a); k++) {
           const SdEdge e = F.out(a, k);
           const int64_t v = D.S1[F.cs(i + 1, e.other - i1s, j, sb)];
           if (!fin(v)) continue;
-          upd(ps, psk, v + e.cost + mlb, (1u << 4) | (uint32_t)k);
+          upd(ps, v + e.cost + mlb);
           TERM(2);
         }
         for (int k = 0; k < F.nin(b); k++) {
           const SdEdge e = F.in(b, k);
           const int64_t v = D.S1[F.cs(i, sa, j - 1, e.other - js)];
           if (!fin(v)) continue;
-          upd(ps, psk, v + e.cost + mlb, (2u << 4) | (uint32_t)k);
+          upd(ps, v + e.cost + mlb);
           TERM(2);
         }
       }
-      settle(ps, psk);
+      ps = settle(ps);
       int64_t s1 = ps;
-      uint32_t s1k = psk;
-      if (fin(Bs[s])) upd(s1, s1k, Bs[s], 0u);
+      if (fin(Bs[s])) upd(s1, Bs[s]);
       D.S1[cell + s] = s1;
-      D.S1k[cell + s] = s1k;
       PSs[s] = ps;
     }
   }
@@ -1079,21 +911,13 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tm |= 1 << t;
       }
       int64_t qv[6];
-      uint32_t qk[6];
+#pragma unroll
+      for (int t = 0; t < 6; t++) qv[t] = SD_INF;
+      if (tm) q_slot<G, COUNT>(F, D, P, T, sub, a0 + sa, b0 + sb, i, sa, j, sb, tm, qv, ops, GS);
 #pragma unroll
       for (int t = 0; t < 6; t++) {
-        qv[t] = SD_INF;
-        qk[t] = KEY_NONE;
-      }
-      if (tm) q_slot<G, COUNT>(F, D, P, T, sub, a0 + sa, b0 + sb, i, sa, j, sb, tm, qv, qk, ops, GS);
-#pragma unroll
-      for (int t = 0; t < 6; t++) {
-        if (tm) seg_lexmin<G>(qv[t], qk[t]);
-        settle(qv[t], qk[t]);
-        if (ok && sub == t % G) {
-          D.Q[(int64_t)(rcell + s) * 6 + t] = qv[t];
-          D.Qk[(int64_t)(rcell + s) * 6 + t] = qk[t];
-        }
+        if (tm) seg_min<G>(qv[t]);
+        if (ok && sub == t % G) D.Q[(int64_t)(rcell + s) * 6 + t] = settle(qv[t]);
       }
     }
     if (COUNT && active && ops) atomicAdd(&ops_out[dsel], ops);
@@ -1114,10 +938,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 #pragma unroll
       for (int t = 0; t < 6; t++)
         if (((im >> c_pair5[t]) & 1) && ((om >> c_pair3[t]) & 1)) tm |= 1 << t;
-      if (!tm && sub < 6) {  // no outer type can close (x, y)
-        D.Q[(int64_t)(rcell + s) * 6 + sub] = SD_INF;
-        D.Qk[(int64_t)(rcell + s) * 6 + sub] = KEY_NONE;
-      }
+      if (!tm && sub < 6) D.Q[(int64_t)(rcell + s) * 6 + sub] = SD_INF;  // no outer type closes (x, y)
     }
     tms |= (uint32_t)tm << (6 * s);
   }
@@ -1152,12 +973,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const int o_dsel = __shfl_sync(FULL, dsel, src), o_i = __shfl_sync(FULL, i, src);
     const int o_a0 = __shfl_sync(FULL, a0, src), o_b0 = __shfl_sync(FULL, b0, src);
     int64_t qv[6];
-    uint32_t qk[6];
 #pragma unroll
-    for (int t = 0; t < 6; t++) {
-      qv[t] = SD_INF;
-      qk[t] = KEY_NONE;
-    }
+    for (int t = 0; t < 6; t++) qv[t] = SD_INF;
     const SdDesign &Do = designs[o_dsel];
     const int sa = s_k / SD_W, sb = s_k % SD_W;
     if (tm_k) {
@@ -1169,7 +986,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       Fo.on = Do.out_cnt;
       Fo.in_ = Do.in_cnt;
       Fo.H = Do.H;
-      Fo.Hk = Do.Hk;
       Fo.V = Do.V;
       Fo.lay = Do.layer;
       Fo.fo = Do.fo;
@@ -1177,17 +993,13 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       Fo.fi = Do.fi;
       Fo.fi_off = Do.fi_off;
       q_slot<G, COUNT>(Fo, Do, P, T, sub, o_a0 + sa, o_b0 + sb, o_i, sa, o_i + g, sb, tm_k, qv,
-                       qk, ops, s_gap[(threadIdx.x >> 5) * NGW + go_k]);
+                       ops, s_gap[(threadIdx.x >> 5) * NGW + go_k]);
     }
     const int o_rcell = ((g & (SD_RING - 1)) * (Do.n + 1) + o_i) * SD_SLOTS;
 #pragma unroll
     for (int t = 0; t < 6; t++) {
-      if (__any_sync(FULL, (tm_k >> t) & 1)) seg_lexmin<G>(qv[t], qk[t]);
-      settle(qv[t], qk[t]);
-      if (tm_k && sub == t % G) {
-        Do.Q[(int64_t)(o_rcell + s_k) * 6 + t] = qv[t];
-        Do.Qk[(int64_t)(o_rcell + s_k) * 6 + t] = qk[t];
-      }
+      if (__any_sync(FULL, (tm_k >> t) & 1)) seg_min<G>(qv[t]);
+      if (tm_k && sub == t % G) Do.Q[(int64_t)(o_rcell + s_k) * 6 + t] = settle(qv[t]);
     }
     if (COUNT && tm_k && ops) atomicAdd(&ops_out[o_dsel], ops);
     ops = 0;
@@ -1195,31 +1007,25 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 }
 
 // ---------------------------------------------------------------------------
-// exterior suffix values (Sec. 5 final-column exterior DP), one block per
-// design; key: unpaired out-edge index, or KEY_SPLIT | b*8 + type
+// exterior suffix values (Sec. 5 final-column exterior DP), one block per design
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_exterior(const SdDesign *__restrict__ designs,
                                                   const SdParams *__restrict__ Pp) {
   const SdDesign &D = designs[blockIdx.x];
   const SdParams &P = *Pp;
   __shared__ int64_t smv[8];
-  __shared__ uint32_t smk[8];
   Lat G(D);
   const int n = D.n, N = D.N;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    D.Ext[N - 1] = 0;
-    D.Extk[N - 1] = KEY_NONE;
-  }
+  if (threadIdx.x == 0) D.Ext[N - 1] = 0;
   __syncthreads();
   for (int k = n - 1; k >= 0; k--) {
     for (int a = G.lstart(k); a < G.lstart(k + 1); a++) {
       int64_t bv = SD_INF;
-      uint32_t bk = KEY_NONE;
       if ((int)threadIdx.x < G.nout(a)) {
         const SdEdge e = G.out(a, threadIdx.x);
         const int64_t x = D.Ext[e.other];
-        if (fin(x)) upd(bv, bk, x + e.cost, threadIdx.x);
+        if (fin(x)) upd(bv, x + e.cost);
       }
       for (int b = G.lstart(k + 1) + threadIdx.x; b < N; b += blockDim.x) {
         const int lb = G.layer(b);
@@ -1229,20 +1035,15 @@ __global__ void __launch_bounds__(256) k_exterior(const SdDesign *__restrict__ d
         const int64_t cs = G.slot(a, b, k, lb) * 6;
         for (int t = 0; t < 6; t++) {
           const int64_t v = D.V[cs + t];
-          if (fin(v)) upd(bv, bk, v + fx(P.au[t]) + eb, KEY_SPLIT | ((uint32_t)b << 3) | t);
+          if (fin(v)) upd(bv, v + fx(P.au[t]) + eb);
         }
       }
-      warp_lexmin(bv, bk);
-      if (lane == 0) {
-        smv[w] = bv;
-        smk[w] = bk;
-      }
+      warp_min(bv);
+      if (lane == 0) smv[w] = bv;
       __syncthreads();
       if (threadIdx.x == 0) {
-        for (int q = 1; q < (int)(blockDim.x >> 5); q++) upd(bv, bk, smv[q], smk[q]);
-        settle(bv, bk);
-        D.Ext[a] = bv;
-        D.Extk[a] = bk;
+        for (int q = 1; q < (int)(blockDim.x >> 5); q++) upd(bv, smv[q]);
+        D.Ext[a] = settle(bv);
       }
       __syncthreads();
     }
@@ -1250,9 +1051,114 @@ __global__ void __launch_bounds__(256) k_exterior(const SdDesign *__restrict__ d
 }
 
 // ---------------------------------------------------------------------------
-// traceback: follows the stored canonical keys (one thread per design) and
-// re-checks every step's value, accumulating the loop energies and codon costs
+// traceback (Sec. 5), one block per design.  The fill keeps values only, so
+// every step re-derives its canonical choice from the full tables: the first
+// option, in a fixed enumeration order, whose value equals the cell's value
+// (exact integer equality).  The orders:
+//   exterior  unpaired out-edge by label, then branch (b ascending, type)
+//   V_t(a,b)  for each in-edge of b with the pair's 3' label, in in-edge
+//             order: hairpin (special lengths: interior paths in label order;
+//             else (first, last) loop labels), two-loops by (l1+l2, l1, c, d,
+//             inner type, left side, right side), multiloop
+//   B         smallest pair type
+//   S2        edge extension (in-edge order), then candidate split at the
+//             smallest state c of C_b
+//   S1        direct branch, left peel (out-edge order), right peel (in-edge
+//             order), two-branch value
+//   sides     (first, last) labels; the gap inside by the greedy label order
+// Thread 0 walks the structure and owns the work list; the searches over
+// many options (exterior branches, two-loops, candidate splits) use the whole
+// block and a block-wide minimum of the option's position in the order.
 // ---------------------------------------------------------------------------
+constexpr int TB_THREADS = 256;
+constexpr unsigned long long NO_OPTION = ~0ull;
+
+__device__ unsigned long long block_min(unsigned long long v, unsigned long long *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(FULL, v, o);
+    v = u < v ? u : v;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < TB_THREADS / 32 ? red[lane] : NO_OPTION;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(FULL, v, o);
+      v = u < v ? u : v;
+    }
+    if (lane == 0) red[TB_THREADS / 32] = v;
+  }
+  __syncthreads();
+  v = red[TB_THREADS / 32];
+  __syncthreads();
+  return v;
+}
+
+// Unpaired sides of a two-loop: the (first, last) label descriptions of the
+// paths x -> y of len edges and their minimum costs.  key: len 0 -> 0; len 1
+// -> the label; len >= 2 -> first*4 + last (a DFA has one 2-edge path per
+// label pair).  Descriptors come in increasing key order.
+struct Sides {
+  int cnt;
+  uint8_t key[16], first[16], last[16];
+  int64_t cost[16];
+};
+
+__device__ void side_descs(const Lat &G, int x, int y, int len, Sides &S) {
+  S.cnt = 0;
+  if (len == 0) {
+    if (x == y) {
+      S.key[0] = S.first[0] = S.last[0] = 0;
+      S.cost[0] = 0;
+      S.cnt = 1;
+    }
+    return;
+  }
+  if (len == 1) {
+    for (int k = 0; k < G.nout(x); k++) {
+      const SdEdge e = G.out(x, k);
+      if (e.other != y) continue;
+      S.key[S.cnt] = S.first[S.cnt] = S.last[S.cnt] = (uint8_t)e.label;
+      S.cost[S.cnt++] = e.cost;
+    }
+    return;
+  }
+  if (len == 2) {
+    for (int k = 0; k < G.nout(x); k++) {
+      const SdEdge e = G.out(x, k);
+      for (int k2 = 0; k2 < G.nout(e.other); k2++) {
+        const SdEdge e2 = G.out(e.other, k2);
+        if (e2.other != y) continue;
+        S.key[S.cnt] = (uint8_t)(e.label * 4 + e2.label);
+        S.first[S.cnt] = (uint8_t)e.label;
+        S.last[S.cnt] = (uint8_t)e2.label;
+        S.cost[S.cnt++] = e.cost + e2.cost;
+      }
+    }
+    return;
+  }
+  for (int k = 0; k < G.nout(x); k++) {
+    const SdEdge e = G.out(x, k);  // out-edges are stored by label
+    for (int l = 0; l < 4; l++) {
+      int64_t best = SD_INF;
+      for (int q = 0; q < G.nin(y); q++) {
+        const SdEdge ei = G.in(y, q);
+        if (ei.label != l) continue;
+        const int64_t h = G.Hp(e.other, ei.other);
+        if (fin(h)) upd(best, e.cost + h + ei.cost);
+      }
+      if (!fin(best)) continue;
+      S.key[S.cnt] = (uint8_t)(e.label * 4 + l);
+      S.first[S.cnt] = (uint8_t)e.label;
+      S.last[S.cnt] = (uint8_t)l;
+      S.cost[S.cnt++] = best;
+    }
+  }
+}
+
 struct Tb {
   const SdDesign &D;
   const SdParams &P;
@@ -1284,7 +1190,10 @@ struct Tb {
     s[3] = t;
   }
   __device__ void set_pair(int pi, int pj) {
-    if (D.structure[pi] != '.' || D.structure[pj] != '.') err = 4;
+    if (pi < 0 || pj >= D.n || D.structure[pi] != '.' || D.structure[pj] != '.') {
+      err = 4;
+      return;
+    }
     D.structure[pi] = '(';
     D.structure[pj] = ')';
   }
@@ -1308,305 +1217,476 @@ struct Tb {
       if (!moved) err = 5;
     }
   }
-  // realise the unpaired side x -> y of len edges with first / last labels
-  // f / l; returns its cost (+inf if it does not exist)
-  __device__ int64_t side(int x, int y, int len, int f, int l) {
-    if (len == 0) return x == y ? 0 : SD_INF;
+  // realise the unpaired side x -> y of len edges with descriptor key `key`
+  // and cost `cost` (as listed by side_descs)
+  __device__ void side(int x, int y, int len, int key, int64_t cost) {
+    if (len == 0) {
+      if (x != y) err = 6;
+      return;
+    }
+    const int f = len == 1 ? key : key >> 2, l = key & 3;
     const int k1 = G.out_with_label(x, f);
-    if (k1 < 0) return SD_INF;
+    if (k1 < 0) {
+      err = 6;
+      return;
+    }
     const SdEdge e1 = G.out(x, k1);
     if (len == 1) {
-      if (e1.other != y) return SD_INF;
-      emit(x, e1.label, e1.cost);
-      return e1.cost;
+      if (e1.other != y || e1.cost != cost) err = 6;
+      else emit(x, e1.label, e1.cost);
+      return;
     }
     if (len == 2) {
       const int k2 = G.out_with_label(e1.other, l);
-      if (k2 < 0) return SD_INF;
+      if (k2 < 0 || G.out(e1.other, k2).other != y) {
+        err = 6;
+        return;
+      }
       const SdEdge e2 = G.out(e1.other, k2);
-      if (e2.other != y) return SD_INF;
       emit(x, e1.label, e1.cost);
       emit(e1.other, e2.label, e2.cost);
-      return e1.cost + e2.cost;
-    }
-    int64_t best = SD_INF;
-    for (int q = 0; q < G.nin(y); q++) {
-      const SdEdge ei = G.in(y, q);
-      if (ei.label != l) continue;
-      const int64_t h = G.Hp(e1.other, ei.other);
-      if (fin(h)) best = min(best, e1.cost + h + ei.cost);
+      return;
     }
     for (int q = 0; q < G.nin(y); q++) {
       const SdEdge ei = G.in(y, q);
       if (ei.label != l) continue;
       const int64_t h = G.Hp(e1.other, ei.other);
-      if (fin(h) && e1.cost + h + ei.cost == best) {
+      if (fin(h) && e1.cost + h + ei.cost == cost) {
         emit(x, e1.label, e1.cost);
         gap(e1.other, ei.other);
         emit(ei.other, ei.label, ei.cost);
-        return best;
+        return;
       }
     }
-    return SD_INF;
+    err = 6;
   }
-
-  __device__ void trace_V(int a, int b, int t) {
-    const int la = G.layer(a), lb = G.layer(b);
-    const int64_t s = G.slot(a, b, la, lb);
-    const int64_t v = D.V[s * 6 + t];
-    const uint32_t key = D.Vk[s * 6 + t];
-    const int kx = G.out_with_label(a, c_pair5[t]);
-    const int ky = key >> 27;
-    if (!fin(v) || kx < 0 || ky >= G.nin(b)) {
-      err = 7;
-      return;
-    }
-    const SdEdge ex = G.out(a, kx), ey = G.in(b, ky);
-    const int a1 = ex.other, b1 = ey.other;
-    const int lx = la + 1, ly = lb - 1, L = ly - lx;
-    set_pair(la, lb - 1);
-    emit(a, ex.label, ex.cost);
-    emit(b1, ey.label, ey.cost);
-    const uint32_t q = key & KEY_QMASK;
-    const int cls = q >> 25;
-    int64_t got = SD_INF;
-    if (cls == 0) {  // hairpin
-      if (L == 3 || L == 4 || L == 6) {
-        int x = a1;
-        int64_t c = 0;
-        for (int k = 0; k < L && x >= 0; k++) {
-          const int lab = (q >> (2 * (L - 1 - k))) & 3;
-          const int kk = G.out_with_label(x, lab);
-          if (kk < 0) {
-            x = -1;
-            break;
+  // hairpin closed by type t with interior path a1 -> b1 of L edges and value
+  // target; realises the first attaining option and returns 1, else 0
+  __device__ int hairpin(int a1, int b1, int t, int L, int64_t target) {
+    if (L < 3) return 0;
+    if (L == 3 || L == 4 || L == 6) {
+      // interior paths in label order (depth-first over out-edges by label)
+      int st[8], kk[8], ed[8];
+      int64_t cst[8];
+      uint32_t labs[8];
+      int depth = 0;
+      st[0] = a1;
+      kk[0] = 0;
+      cst[0] = 0;
+      labs[0] = 0;
+      while (depth >= 0) {
+        if (depth == L) {
+          const int e = hairpin_seq_e(P, D.hp_len, t, labs[L], L);
+          if (fx(e) + cst[L] == target) {
+            for (int q = 0; q < L; q++) {
+              const SdEdge x = G.out(st[q], ed[q]);
+              emit(st[q], x.label, x.cost);
+            }
+            energy += e;
+            return 1;
           }
-          const SdEdge e = G.out(x, kk);
-          emit(x, e.label, e.cost);
-          c += e.cost;
-          x = e.other;
+          depth--;
+          continue;
         }
-        if (x == b1) {
-          const int e = hairpin_seq_e(P, D.hp_len, t, q & 0xfff, L);
-          energy += e;
-          got = fx(e) + c;
+        const int v = st[depth];
+        const int k = kk[depth]++;
+        if (k >= G.nout(v)) {
+          depth--;
+          continue;
         }
-      } else {
-        const int f = (q >> 2) & 3, l = q & 3;
-        const int64_t c = side(a1, b1, L, f, l);
-        if (fin(c)) {
-          const int e = hairpin_generic_e(P, D.hp_len, t, L, f, l);
-          energy += e;
-          got = fx(e) + c;
-        }
+        const SdEdge e = G.out(v, k);
+        if (depth + 1 == L ? e.other != b1 : !fin(G.Hp(e.other, b1))) continue;
+        ed[depth] = k;
+        st[depth + 1] = e.other;
+        cst[depth + 1] = cst[depth] + e.cost;
+        labs[depth + 1] = (labs[depth] << 2) | (uint32_t)e.label;
+        kk[depth + 1] = 0;
+        depth++;
       }
-    } else if (cls == 1) {  // two-loop
-      const int l = (q >> 20) & 31, l1 = (q >> 15) & 31, l2 = l - l1;
-      const int cs = (q >> 13) & 3, ds = (q >> 11) & 3, ti = (q >> 8) & 7;
-      const int fL = (q >> 6) & 3, lL = (q >> 4) & 3, fR = (q >> 2) & 3, lR = q & 3;
-      const int lc = lx + l1, ld = ly - l2;
-      if (l2 >= 0 && ld - lc >= 5 && ti < 6) {
-        const int c = G.lstart(lc) + cs, d = G.lstart(ld) + ds;
-        const int64_t cl = side(a1, c, l1, fL, lL);
-        const int64_t cr = side(d, b1, l2, fR, lR);
-        const int64_t vi = G.Vt(c, d, ti);
-        if (fin(cl) && fin(cr) && fin(vi)) {
-          const int e = twoloop_e(P, t, ti, l1, l2, fL, lL, fR, lR);
-          energy += e;
-          got = fx(e) + cl + cr + vi;
-          push(1, c, d, ti);
-        }
-      }
-    } else {  // multiloop
-      const int64_t s2 = G.S2(a1, b1);
-      if (fin(s2)) {
-        energy += P.mlclosing + P.mlintern + P.au[t];
-        got = s2 + fx(P.mlclosing + P.mlintern + P.au[t]);
-        push(3, a1, b1, 0);
+      return 0;
+    }
+    Sides S;
+    side_descs(G, a1, b1, L, S);
+    for (int q = 0; q < S.cnt; q++) {
+      const int e = hairpin_generic_e(P, D.hp_len, t, L, S.first[q], S.last[q]);
+      if (fx(e) + S.cost[q] == target) {
+        side(a1, b1, L, S.key[q], S.cost[q]);
+        energy += e;
+        return 1;
       }
     }
-    if (!fin(got) || got + ex.cost + ey.cost != v) err = 8;
-  }
-  __device__ void trace_B(int a, int b) {
-    const int64_t s = G.slot(a, b, G.layer(a), G.layer(b));
-    const int t = D.Bk[s];
-    const int64_t v = t < 6 ? G.Vt(a, b, t) : SD_INF;
-    if (!fin(v) || v + fx(P.mlintern + P.au[t]) != D.Bv[s]) {
-      err = 9;
-      return;
-    }
-    energy += P.mlintern + P.au[t];
-    trace_V(a, b, t);
-  }
-  __device__ void trace_S2(int a, int b) {
-    const int la = G.layer(a);
-    while (!err) {
-      const int lb = G.layer(b);
-      if (lb <= la) {
-        err = 10;
-        return;
-      }
-      const int64_t s = G.slot(a, b, la, lb);
-      const int64_t v = D.S2[s];
-      const uint32_t key = D.S2k[s];
-      if (!fin(v)) {
-        err = 10;
-        return;
-      }
-      if (key < KEY_SPLIT) {
-        if ((int)key >= G.nin(b)) {
-          err = 10;
-          return;
-        }
-        const SdEdge e = G.in(b, key);
-        const int64_t x = G.S2(a, e.other);
-        if (!fin(x) || x + e.cost + fx(P.mlbase) != v) {
-          err = 10;
-          return;
-        }
-        emit(e.other, e.label, e.cost);
-        energy += P.mlbase;
-        b = e.other;
-        continue;
-      }
-      const int c = key & (KEY_SPLIT - 1);
-      if (c >= D.N) {
-        err = 11;
-        return;
-      }
-      const int64_t x = G.S1(a, c);
-      const int lc = G.layer(c);
-      const int64_t bc = (lb - lc >= 5) ? D.Bv[G.slot(c, b, lc, lb)] : SD_INF;
-      if (!fin(x) || !fin(bc) || x + bc != v) {
-        err = 11;
-        return;
-      }
-      push(2, a, c, 0);
-      push(4, c, b, 0);
-      return;
-    }
-  }
-  __device__ void trace_S1(int a, int b) {
-    const int64_t mlb = fx(P.mlbase);
-    while (!err) {
-      const int la = G.layer(a), lb = G.layer(b);
-      if (lb <= la) {
-        err = 12;
-        return;
-      }
-      const int64_t s = G.slot(a, b, la, lb);
-      const int64_t v = D.S1[s];
-      const uint32_t key = D.S1k[s];
-      if (!fin(v)) {
-        err = 12;
-        return;
-      }
-      const int cls = key >> 4, k = key & 15;
-      if (cls == 0) {
-        if (D.Bv[s] != v) err = 12;
-        else trace_B(a, b);
-        return;
-      }
-      if (cls == 1) {
-        if (k >= G.nout(a)) {
-          err = 13;
-          return;
-        }
-        const SdEdge e = G.out(a, k);
-        const int64_t x = G.S1(e.other, b);
-        if (!fin(x) || x + e.cost + mlb != v) {
-          err = 13;
-          return;
-        }
-        emit(a, e.label, e.cost);
-        energy += P.mlbase;
-        a = e.other;
-        continue;
-      }
-      if (cls == 2) {
-        if (k >= G.nin(b)) {
-          err = 13;
-          return;
-        }
-        const SdEdge e = G.in(b, k);
-        const int64_t x = G.S1(a, e.other);
-        if (!fin(x) || x + e.cost + mlb != v) {
-          err = 13;
-          return;
-        }
-        emit(e.other, e.label, e.cost);
-        energy += P.mlbase;
-        b = e.other;
-        continue;
-      }
-      if (D.S2[s] != v) err = 13;
-      else trace_S2(a, b);
-      return;
-    }
-  }
-  __device__ void run() {
-    const int N = D.N;
-    int a = 0;
-    const int tstate = N - 1;
-    if (!fin(D.Ext[0])) {
-      err = 14;
-      return;
-    }
-    while (a != tstate && !err) {
-      const int64_t v = D.Ext[a];
-      const uint32_t key = D.Extk[a];
-      if (key < KEY_SPLIT) {
-        if ((int)key >= G.nout(a)) {
-          err = 15;
-          break;
-        }
-        const SdEdge e = G.out(a, key);
-        if (D.Ext[e.other] + e.cost != v) {
-          err = 15;
-          break;
-        }
-        emit(a, e.label, e.cost);
-        a = e.other;
-      } else {
-        const int b = (key & (KEY_SPLIT - 1)) >> 3, t = key & 7;
-        const int64_t x = (b < N && t < 6) ? G.Vt(a, b, t) : SD_INF;
-        if (!fin(x) || x + fx(P.au[t]) + D.Ext[b] != v) {
-          err = 15;
-          break;
-        }
-        energy += P.au[t];
-        push(1, a, b, t);
-        a = b;
-      }
-    }
-    while (sp > 0 && !err) {
-      const int32_t *s = D.tb_stack + 4 * --sp;
-      const int type = s[0], x = s[1], y = s[2], t = s[3];
-      if (type == 1) trace_V(x, y, t);
-      else if (type == 2) trace_S1(x, y);
-      else if (type == 3) trace_S2(x, y);
-      else trace_B(x, y);
-    }
-    for (int k = 0; k < D.n && !err; k++)
-      if (D.mrna[k] == 0) err = 16;
+    return 0;
   }
 };
 
-__global__ void k_traceback(const SdDesign *__restrict__ designs, const SdParams *__restrict__ Pp) {
+// (l1+l2, l1) pairs of the two-loops in enumeration order: pair u has
+// l = floor((sqrt(8u+1)-1)/2), l1 = u - l(l+1)/2
+constexpr int TL_PAIRS = (SD_MAXTWO + 1) * (SD_MAXTWO + 2) / 2;
+
+// Block-wide search for the first two-loop closing pair type t over the
+// interior a1 -> b1 with value target.  Returns the option's position in
+// the enumeration order, ((u*4 + cs*2 + ds)*6 + ti)*256 + left key*16 + right
+// key, or NO_OPTION.
+__device__ unsigned long long search_twoloop(const Lat &G, const SdParams &P, int a1, int b1, int t,
+                                             int64_t target, unsigned long long *red) {
+  unsigned long long best = NO_OPTION;
+  const int lx = G.layer(a1), ly = G.layer(b1);
+  for (int u4 = threadIdx.x; u4 < TL_PAIRS * 4; u4 += TB_THREADS) {
+    const int u = u4 >> 2, cs = (u4 >> 1) & 1, ds = u4 & 1;
+    int l = 0;
+    while ((l + 1) * (l + 2) / 2 <= u) l++;
+    const int l1 = u - l * (l + 1) / 2, l2 = l - l1;
+    const int lc = lx + l1, ld = ly - l2;
+    if (ld - lc < 5) continue;
+    if (cs >= G.lstart(lc + 1) - G.lstart(lc) || ds >= G.lstart(ld + 1) - G.lstart(ld)) continue;
+    const int c = G.lstart(lc) + cs, d = G.lstart(ld) + ds;
+    const int64_t hl = G.Hp(a1, c), hr = G.Hp(d, b1);
+    if (!fin(hl) || !fin(hr)) continue;
+    const int64_t cell = G.slot(c, d, lc, ld) * 6;
+    int64_t vv[6], vmin = SD_INF;
+    for (int ti = 0; ti < 6; ti++) {
+      vv[ti] = G.D.V[cell + ti];
+      if (fin(vv[ti])) upd(vmin, vv[ti]);
+    }
+    // no option of this unit can reach the target: every side costs at
+    // least the minimum path cost, every loop at least lb2
+    const int64_t floor = hl + hr + fx(P.lb2[l1][l2]);
+    if (!fin(vmin) || vmin + floor > target) continue;
+    Sides SL, SR;
+    side_descs(G, a1, c, l1, SL);
+    side_descs(G, d, b1, l2, SR);
+    bool found = false;
+    for (int ti = 0; ti < 6 && !found; ti++) {
+      if (!fin(vv[ti]) || vv[ti] + floor > target) continue;
+      for (int p = 0; p < SL.cnt && !found; p++)
+        for (int r = 0; r < SR.cnt && !found; r++) {
+          const int e = sd_twoloop_energy(P, t, ti, l1, l2, SL.first[p], SL.last[p], SR.first[r],
+                                          SR.last[r]);
+          if (vv[ti] + fx(e) + SL.cost[p] + SR.cost[r] == target) {
+            const unsigned long long pos =
+                ((((unsigned long long)u4) * 6 + ti) * 256) + SL.key[p] * 16 + SR.key[r];
+            best = pos < best ? pos : best;
+            found = true;
+          }
+        }
+    }
+  }
+  return block_min(best, red);
+}
+
+__global__ void __launch_bounds__(TB_THREADS) k_traceback(const SdDesign *__restrict__ designs,
+                                                          const SdParams *__restrict__ Pp) {
   const SdDesign &D = designs[blockIdx.x];
+  const SdParams &P = *Pp;
+  __shared__ unsigned long long red[TB_THREADS / 32 + 1];
+  __shared__ int cmd[6];
+  __shared__ int64_t cval[2];
   for (int k = threadIdx.x; k < D.n; k += blockDim.x) {
     D.mrna[k] = 0;
     D.structure[k] = '.';
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  D.mrna[D.n] = 0;
-  D.structure[D.n] = 0;
-  Tb tb(D, *Pp);
-  tb.run();
-  D.tb[0] = tb.energy;
-  D.tb[1] = tb.pathcost;
-  D.tb[2] = tb.err;
+  const bool t0 = threadIdx.x == 0;
+  Tb tb(D, P);
+  Lat &G = tb.G;
+  const int N = D.N;
+  if (t0) {
+    D.mrna[D.n] = 0;
+    D.structure[D.n] = 0;
+    if (!fin(D.Ext[0])) tb.err = 14;
+  }
+  // ---- exterior walk from the source ----
+  int a = 0;
+  for (int it = 0; it <= D.n + 1; it++) {
+    if (t0) {
+      cmd[0] = 0;  // 0 done, 1 moved, 2 search branches
+      if (a != N - 1 && !tb.err) {
+        const int64_t v = D.Ext[a];
+        cmd[0] = 2;
+        for (int k = 0; k < G.nout(a); k++) {
+          const SdEdge e = G.out(a, k);
+          const int64_t x = D.Ext[e.other];
+          if (fin(x) && x + e.cost == v) {
+            tb.emit(a, e.label, e.cost);
+            a = e.other;
+            cmd[0] = 1;
+            break;
+          }
+        }
+      }
+      cmd[1] = a;
+    }
+    __syncthreads();
+    const int c0 = cmd[0];
+    a = cmd[1];
+    __syncthreads();
+    if (c0 == 0) break;
+    if (c0 == 1) continue;
+    // branch (b ascending, type) with V_t(a,b) + AU(t) + Ext(b) = Ext(a)
+    unsigned long long best = NO_OPTION;
+    const int la = G.layer(a);
+    const int64_t v = D.Ext[a];
+    for (int b = G.lstart(la + 1) + threadIdx.x; b < N; b += TB_THREADS) {
+      const int lb = G.layer(b);
+      if (lb - la < 5) continue;
+      const int64_t eb = D.Ext[b];
+      if (!fin(eb)) continue;
+      const int64_t cs = G.slot(a, b, la, lb) * 6;
+      for (int t = 0; t < 6; t++) {
+        const int64_t x = D.V[cs + t];
+        if (fin(x) && x + fx(P.au[t]) + eb == v) {
+          const unsigned long long pos = (unsigned long long)b * 8 + t;
+          best = pos < best ? pos : best;
+          break;
+        }
+      }
+    }
+    best = block_min(best, red);
+    if (t0) {
+      if (best == NO_OPTION) {
+        tb.err = 15;
+      } else {
+        const int b = (int)(best >> 3), t = (int)(best & 7);
+        tb.energy += P.au[t];
+        tb.push(1, a, b, t);
+        a = b;
+      }
+      cmd[1] = a;
+    }
+    __syncthreads();
+    a = cmd[1];
+    __syncthreads();
+  }
+  // ---- the work list: 1 V_t(x,y), 2 S1(x,y), 3 S2(x,y), 4 B(x,y) ----
+  const int bound = 8 * D.n + 64;
+  for (int it = 0; it < bound; it++) {
+    if (t0) {
+      cmd[0] = 0;
+      if (!tb.err && tb.sp > 0) {
+        const int32_t *s = D.tb_stack + 4 * --tb.sp;
+        cmd[0] = s[0];
+        cmd[1] = s[1];
+        cmd[2] = s[2];
+        cmd[3] = s[3];
+      }
+      if (it == bound - 1 && cmd[0]) tb.err = 17;
+    }
+    __syncthreads();
+    const int type = cmd[0], x = cmd[1], y = cmd[2], t = cmd[3];
+    __syncthreads();
+    if (type == 0) break;
+    if (type == 4) {  // B(x,y): smallest pair type
+      if (t0) {
+        const int64_t s = G.slot(x, y, G.layer(x), G.layer(y));
+        int tt = 0;
+        for (; tt < 6; tt++) {
+          const int64_t vv = G.Vt(x, y, tt);
+          if (fin(vv) && vv + fx(P.mlintern + P.au[tt]) == D.Bv[s]) break;
+        }
+        if (tt == 6) {
+          tb.err = 9;
+        } else {
+          tb.energy += P.mlintern + P.au[tt];
+          tb.push(1, x, y, tt);
+        }
+      }
+      continue;
+    }
+    if (type == 2) {  // S1(x,y): direct < left peel < right peel < S2
+      if (t0) {
+        const int64_t mlb = fx(P.mlbase);
+        int xa = x, yb = y, steps = 0;
+        while (!tb.err) {
+          if (++steps > 2 * D.n + 4) {
+            tb.err = 12;
+            break;
+          }
+          const int la = G.layer(xa), lb = G.layer(yb);
+          if (lb <= la) {
+            tb.err = 12;
+            break;
+          }
+          const int64_t s = G.slot(xa, yb, la, lb);
+          const int64_t v = D.S1[s];
+          if (!fin(v)) {
+            tb.err = 12;
+            break;
+          }
+          if (D.Bv[s] == v) {
+            tb.push(4, xa, yb, 0);
+            break;
+          }
+          int moved = 0;
+          for (int k = 0; k < G.nout(xa) && !moved; k++) {
+            const SdEdge e = G.out(xa, k);
+            const int64_t w = G.S1(e.other, yb);
+            if (fin(w) && w + e.cost + mlb == v) {
+              tb.emit(xa, e.label, e.cost);
+              tb.energy += P.mlbase;
+              xa = e.other;
+              moved = 1;
+            }
+          }
+          for (int k = 0; k < G.nin(yb) && !moved; k++) {
+            const SdEdge e = G.in(yb, k);
+            const int64_t w = G.S1(xa, e.other);
+            if (fin(w) && w + e.cost + mlb == v) {
+              tb.emit(e.other, e.label, e.cost);
+              tb.energy += P.mlbase;
+              yb = e.other;
+              moved = 1;
+            }
+          }
+          if (moved) continue;
+          if (D.S2[s] == v) tb.push(3, xa, yb, 0);
+          else tb.err = 13;
+          break;
+        }
+      }
+      continue;
+    }
+    if (type == 3) {  // S2(x,y): edge extensions, then the candidate split
+      if (t0) {
+        const int64_t mlb = fx(P.mlbase);
+        int yb = y, steps = 0;
+        cmd[4] = -1;
+        while (!tb.err) {
+          if (++steps > D.n + 2) {
+            tb.err = 10;
+            break;
+          }
+          const int la = G.layer(x), lb = G.layer(yb);
+          const int64_t v = lb > la ? D.S2[G.slot(x, yb, la, lb)] : SD_INF;
+          if (!fin(v)) {
+            tb.err = 10;
+            break;
+          }
+          int moved = 0;
+          for (int k = 0; k < G.nin(yb); k++) {
+            const SdEdge e = G.in(yb, k);
+            const int64_t w = G.S2(x, e.other);
+            if (fin(w) && w + e.cost + mlb == v) {
+              tb.emit(e.other, e.label, e.cost);
+              tb.energy += P.mlbase;
+              yb = e.other;
+              moved = 1;
+              break;
+            }
+          }
+          if (moved) continue;
+          cmd[4] = yb;
+          cval[0] = v;
+          break;
+        }
+      }
+      __syncthreads();
+      const int yb = cmd[4];
+      const int64_t v = cval[0];
+      __syncthreads();
+      if (yb < 0) continue;
+      // smallest candidate c of C_yb with S1(x,c) + B(c,yb) = S2(x,yb)
+      unsigned long long best = NO_OPTION;
+      const int lx = G.layer(x);
+      const int cnt = D.cand_cap ? min(D.cand_cnt[yb], D.cand_cap[yb]) : D.cand_cnt[yb];
+      const int64_t off = D.cand_off[yb];
+      for (int k = threadIdx.x; k < cnt; k += TB_THREADS) {
+        const int c = D.cand_c[off + k];
+        if (G.layer(c) <= lx) continue;
+        const int64_t w = G.S1(x, c);
+        if (fin(w) && w + D.cand_B[off + k] == v) best = (unsigned long long)c < best ? c : best;
+      }
+      best = block_min(best, red);
+      if (t0) {
+        if (best == NO_OPTION) {
+          tb.err = 11;
+        } else {
+          tb.push(2, x, (int)best, 0);
+          tb.push(4, (int)best, yb, 0);
+        }
+      }
+      continue;
+    }
+    // type 1: V_t(x,y)
+    {
+      const int64_t s = G.slot(x, y, G.layer(x), G.layer(y));
+      const int64_t v = D.V[s * 6 + t];
+      const int kx = G.out_with_label(x, c_pair5[t]);
+      if (!fin(v) || kx < 0 || G.layer(y) - G.layer(x) < 5) {
+        if (t0) tb.err = 7;
+        continue;
+      }
+      const SdEdge ex = G.out(x, kx);
+      const int a1 = ex.other;
+      int done = 0;
+      for (int k = 0; k < G.nin(y) && !done; k++) {
+        const SdEdge ey = G.in(y, k);
+        if (ey.label != c_pair3[t]) continue;
+        const int b1 = ey.other;
+        const int L = G.layer(b1) - G.layer(a1);
+        const int64_t target = v - ex.cost - ey.cost;
+        if (t0) cmd[5] = tb.hairpin(a1, b1, t, L, target);
+        __syncthreads();
+        done = cmd[5];
+        __syncthreads();
+        if (!done) {
+          const unsigned long long pos = search_twoloop(G, P, a1, b1, t, target, red);
+          if (pos != NO_OPTION) {
+            done = 1;
+            if (t0) {
+              const int rk = (int)(pos & 15), lk = (int)((pos >> 4) & 15);
+              const int ti = (int)((pos >> 8) % 6);
+              const int u4 = (int)((pos >> 8) / 6), u = u4 >> 2;
+              const int cs = (u4 >> 1) & 1, ds = u4 & 1;
+              int l = 0;
+              while ((l + 1) * (l + 2) / 2 <= u) l++;
+              const int l1 = u - l * (l + 1) / 2, l2 = l - l1;
+              const int lc = G.layer(a1) + l1, ld = G.layer(b1) - l2;
+              const int c = G.lstart(lc) + cs, d = G.lstart(ld) + ds;
+              Sides SL, SR;
+              side_descs(G, a1, c, l1, SL);
+              side_descs(G, d, b1, l2, SR);
+              int p = 0, r = 0;
+              while (p < SL.cnt && SL.key[p] != lk) p++;
+              while (r < SR.cnt && SR.key[r] != rk) r++;
+              if (p == SL.cnt || r == SR.cnt) {
+                tb.err = 8;
+              } else {
+                tb.side(a1, c, l1, lk, SL.cost[p]);
+                tb.side(d, b1, l2, rk, SR.cost[r]);
+                tb.energy += sd_twoloop_energy(P, t, ti, l1, l2, SL.first[p], SL.last[p],
+                                               SR.first[r], SR.last[r]);
+                tb.push(1, c, d, ti);
+              }
+            }
+          }
+        }
+        if (!done && L >= 1) {
+          const int64_t s2 = G.S2(a1, b1);
+          if (fin(s2) && s2 + fx(P.mlclosing + P.mlintern + P.au[t]) == target) {
+            done = 1;
+            if (t0) {
+              tb.energy += P.mlclosing + P.mlintern + P.au[t];
+              tb.push(3, a1, b1, 0);
+            }
+          }
+        }
+        if (done && t0) {
+          tb.set_pair(G.layer(x), G.layer(y) - 1);
+          tb.emit(x, ex.label, ex.cost);
+          tb.emit(b1, ey.label, ey.cost);
+        }
+      }
+      if (!done && t0) tb.err = 8;
+    }
+  }
+  if (t0) {
+    if (!tb.err && tb.sp > 0) tb.err = 17;
+    for (int k = 0; k < D.n && !tb.err; k++)
+      if (D.mrna[k] == 0) tb.err = 16;
+    D.tb[0] = tb.energy;
+    D.tb[1] = tb.pathcost;
+    D.tb[2] = tb.err;
+  }
 }
 
 __global__ void k_clear_cand(const SdDesign *__restrict__ designs) {
@@ -1755,7 +1835,7 @@ extern "C" int sd_k_run(const SdDesign *d_designs, int count, const int *ns, con
   if (events) record(events[1], st);
   k_exterior<<<count, 256, 0, st>>>(d_designs, d_params);
   if (events) record(events[2], st);
-  k_traceback<<<count, 128, 0, st>>>(d_designs, d_params);
+  k_traceback<<<count, TB_THREADS, 0, st>>>(d_designs, d_params);
   if (events) record(events[3], st);
   if (launches) *launches = (int64_t)ns[0] + 3;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;

@@ -211,28 +211,19 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.fi = (SdFlatEdge *)take((L.E > 0 ? L.E : 1) * sizeof(SdFlatEdge));
   d.fi_off = (int32_t *)take((N + 1) * 4);
   d.H = (int64_t *)take(ncell * SD_SLOTS * 8);
-  d.Hk = (uint8_t *)take(ncell * SD_SLOTS);
   d.V = (int64_t *)take(ncell * SD_SLOTS * 6 * 8);
-  d.Vk = (uint32_t *)take(ncell * SD_SLOTS * 6 * 4);
   d.S1 = (int64_t *)take(ncell * SD_SLOTS * 8);
-  d.S1k = (uint32_t *)take(ncell * SD_SLOTS * 4);
   d.S2 = (int64_t *)take(ncell * SD_SLOTS * 8);
-  d.S2k = (uint32_t *)take(ncell * SD_SLOTS * 4);
   d.Bv = (int64_t *)take(ncell * SD_SLOTS * 8);
-  d.Bk = (uint8_t *)take(ncell * SD_SLOTS);
   d.Ihat = (int64_t *)take(ring * 8);
-  d.Ihk = (uint32_t *)take(ring * 4);
   d.IL = (int64_t *)take(ring * 8);
-  d.ILk = (uint32_t *)take(ring * 4);
   d.Q = (int64_t *)take(ring * 6 * 8);
-  d.Qk = (uint32_t *)take(ring * 6 * 4);
   d.W = (int64_t *)take(ring * SD_WN * 8);
   d.cand_cnt = (int32_t *)take(N * 4);
   d.cand_off = (int64_t *)take(N * 8);
   d.cand_c = (int32_t *)take((cap > 0 ? cap : 1) * 4);
   d.cand_B = (int64_t *)take((cap > 0 ? cap : 1) * 8);
   d.Ext = (int64_t *)take(N * 8);
-  d.Extk = (uint32_t *)take(N * 4);
   d.mrna = take(n + 1);
   d.structure = take(n + 1);
   d.tb = (int64_t *)take(4 * 8);
@@ -255,6 +246,7 @@ extern "C" int sd_design_noalloc(const sd_energy *energy, const char *protein,
   if (!energy || !protein || !codon_weights || !out || !out->mrna || !out->structure)
     return SD_EINVAL;
   if (!(std::isfinite(lambda) && lambda >= 0.0)) return SD_EINVAL;
+  if (!sd_internal_on_energy_device(energy)) return SD_EINVAL;
   char *mrna = out->mrna, *structure = out->structure;
   FixedLattice &L = g_lat;
   int rc = build_fixed(protein, codon_weights, lambda, L);

@@ -350,3 +350,49 @@ def test_dense_control_full_size(sd, E1):
     plan.free()
     assert dense["objective_fx"] == sparse["objective_fx"]
     assert dense["Z"] > sparse["Z"]
+
+
+def _oracle_job(args):
+    par, prot, w, lam = args
+    o = oracle.run(par, prot, w, lam)
+    return o
+
+
+@pytest.fixture(scope="module")
+def bench_config_batch(par1):
+    """Four 180-250-aa proteins at lambda 4 and 0 and their oracle designs and
+    tables (computed in a spawn pool: the dense oracle takes ~0.5-1 min each)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    lengths, lams = [250, 220, 200, 180], [4.0, 0.0, 4.0, 0.0]
+    seeds = [300 + k for k in range(4)]
+    prots = [inputs.random_protein(A, s) for A, s in zip(lengths, seeds)]
+    ws = np.stack([inputs.random_codon_weights(s) for s in seeds])
+    with cf.ProcessPoolExecutor(4, mp_context=mp.get_context("spawn")) as ex:
+        orc = list(ex.map(_oracle_job, [(par1, p, w, l) for p, w, l in zip(prots, ws, lams)]))
+    return prots, ws, lams, orc
+
+
+@pytest.mark.parametrize("margin", [2.0, 0.05])
+def test_bench_configuration_against_the_oracle(sd, E1, bench_config_batch, margin):
+    """The launch configuration bench.py times -- fill group 8, candidate lists
+    presized by the shipped predictor, the whole run replayed as one CUDA
+    graph -- element by element against the dense oracle (Thm. 1: every S1,
+    S2, C_b equals the dense D1, D2, C_b) on 180-250-aa designs, on two
+    replays in a row; margin 0.05 leaves the lists too small, so the run is
+    repeated with worst-case room (regrow) and must give the same results."""
+    from paper_2609_32308_b300 import retention
+    prots, ws, lams, orc = bench_config_batch
+    plan = sd.Plan(E1, prots, ws, lams, predictor=retention.load(), margin=margin)
+    plan.group = 8
+    plan.set_graph(True)
+    for rep in range(2):
+        plan.run()
+        res = plan.results()
+        for k in range(len(prots)):
+            compare_design(res[k], orc[k], lams[k])
+            if margin < 1.0:
+                assert res[k]["regrows"] >= 1
+    for k in range(len(prots)):
+        compare_tables(plan, k, orc[k])
+    plan.free()
