@@ -11,15 +11,20 @@ resident in HBM.  The batched form is the predictor-scheduled one: the
 shipped retention predictor presizes the candidate lists, the autotuner picks
 the fill group during the warm-up, and every step replays one CUDA graph.
 "plain" runs the same kernels on a batch of one, one protein per launch
-sequence, without predictor or graph.
-Inputs are seeded and synthetic (amino acids i.i.d. from the Swiss-Prot
-composition, seeded codon weights, seeded Turner-shaped integer tables).
+sequence, without predictor or graph, at the fill group the autotuner picks
+for it.  Inputs are seeded and synthetic (amino acids i.i.d. from the
+Swiss-Prot composition, seeded codon weights, seeded Turner-shaped integer
+tables).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--impl reference]
 
 Prints one JSON line on rank 0.  Under torchrun every rank designs its own B
 proteins (weak scaling, no data-path collective); the time is the max over
-ranks.
+ranks.  Outside the timed region the run also measures the integer add/min
+peak of the GPU (the roofline denominator), the other workloads of the
+measurement plan (925 aa at lambda = 0, the 1,976-aa footprint, a batch-size
+sweep, a mixed-length batch with and without the predicted schedule) and the
+CPU oracle on bounded samples (--no-extras / --no-cpu-baseline skip them).
 """
 from __future__ import annotations
 
@@ -42,6 +47,12 @@ LENGTH = 925
 LAMBDA = 4.0
 ENERGY_SEED = 1
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the fill per
+# layer pair, from a one-launch ncu capture of a small case of the kernel
+# source with this SHA-256, scaled here to a bench launch by its layer pairs
+# (the procedure is in the design notes).  Any other kernel source: null.
+FILL_DRAM = {"sha256": None, "bytes_per_layer_pair": None}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -51,21 +62,22 @@ def parse():
     ap.add_argument("--batch", type=int, default=32)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-aa", type=int, default=80)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other workloads measured after the timed region")
+    ap.add_argument("--sweep", default="1,8,32,64",
+                    help="batch sizes of the 925-aa sweep (extras)")
+    ap.add_argument("--mixed", type=int, default=512,
+                    help="proteins of the mixed-length batch (extras; 0 = skip)")
     ap.add_argument("--no-predictor", action="store_true",
                     help="worst-case candidate room instead of the predictor's")
     ap.add_argument("--dense-control", action="store_true",
                     help="also run the batch once with every finite direct interval "
                          "retained (scalar-dense control) and report its fill time and Z")
-    ap.add_argument("--once", action="store_true",
-                    help="profiling case: build the batch, run it once with --group, read "
-                         "the results; no timing and no JSON line")
-    ap.add_argument("--group", type=int, default=8, help="fill group for --once")
-    ap.add_argument("--length", type=int, default=LENGTH, help="protein length for --once")
+    ap.add_argument("--cpu-sample-aa", type=int, default=80)
     return ap.parse_args()
 
 
-def peaks():
+def peaks_file():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
@@ -73,33 +85,14 @@ def peaks():
         return {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-# ALU peak derived from the unit counts: 148 SMs x 4 SM sub-partitions x 32
-# lanes issue one 32-bit integer instruction per lane per clock.
-SMS, LANES_PER_SM = 148, 128
-
-
-def alu_peak_tops(sm_mhz: float) -> float:
-    return SMS * LANES_PER_SM * sm_mhz * 1e6 / 1e12
-
-
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per fill launch of
-# the default workload, averaged over the 2,775 fill launches of one timed step
-# in one ncu capture (profiles/k_fill_span_traffic_bench_925aa_batch32.md).  The
-# figure belongs to the kernel source with this SHA-256; any other build reports
-# null.
-FILL_TRAFFIC = {"sha256": "0a1b2da8c685b633a6b62fd84ab3d1ea7284634ae813b58223ff204a9466ffee",
-                "bytes_per_launch": 1007323187}
-
-
-def fill_traffic():
+def kernel_sha() -> str | None:
     import hashlib
     src = os.path.join(ROOT, "paper_2609_32308_b300", "csrc", "sd_kernels.cu")
     try:
         with open(src, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+            return hashlib.sha256(f.read()).hexdigest()
     except OSError:
         return None
-    return FILL_TRAFFIC["bytes_per_launch"] if digest == FILL_TRAFFIC["sha256"] else None
 
 
 class Clocks:
@@ -171,13 +164,13 @@ def job_rate(designs_per_rank: int, world: int, steps: int, elapsed_max: float) 
     return designs_per_rank * world * steps / elapsed_max
 
 
-def workload(batch: int, rank: int, length: int = LENGTH):
+def workload(batch: int, rank: int, length: int = LENGTH, lam: float = LAMBDA):
     from paper_2609_32308_b300 import inputs
     import numpy as np
     seeds = shard_seeds(batch, rank)
     prots = [inputs.random_protein(length, s) for s in seeds]
     ws = np.stack([inputs.random_codon_weights(s) for s in seeds])
-    return prots, ws, [LAMBDA] * batch
+    return prots, ws, [lam] * batch
 
 
 def energy_path():
@@ -186,86 +179,184 @@ def energy_path():
     return inputs.energy_file_for_seed(ENERGY_SEED, d)
 
 
-def cpu_baseline(sample_aa: int, cells_per_design: float):
-    """The oracle as it stands, single-threaded, on a bounded sample: one
-    sample_aa-protein at lambda=4.  Its retained cell-update rate is converted
-    to 925-aa designs/s with the 925-aa design's cell-update count (the
-    oracle's cost per cell grows with length, so this overstates it)."""
+def load_energy():
+    import paper_2609_32308_b300 as sd
+    return sd.sd_load_energy(energy_path())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (the baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_series(sizes_1t, sizes_mt, lam=LAMBDA, seed0=424242):
+    """Oracle wall times on seeded proteins: single-threaded at sizes_1t, all
+    host cores (each span's layer pairs in parallel) at sizes_mt."""
     import oracle
     from paper_2609_32308_b300 import inputs
     par = energy_path()
-    prot = inputs.random_protein(sample_aa, 424242)
-    w = inputs.random_codon_weights(424242)
     oracle.build()
-    t0 = time.perf_counter()
-    o = oracle.run(par, prot, w, LAMBDA)
-    dt = time.perf_counter() - t0
-    rate = o.retained_cells / dt
-    return {"value": rate / cells_per_design, "unit": "designs/s", "cores": 1, "kind": "oracle",
-            "sample": f"one {sample_aa}-aa protein at lambda=4 ({dt:.2f} s, "
-                      f"{o.retained_cells} retained cell updates); rate scaled by the "
-                      f"925-aa design's {int(cells_per_design)} cell updates",
-            "cell_updates_per_s": rate, "seconds": dt}
+    cores = os.cpu_count() or 1
+    out = []
+    for threads, sizes in ((1, sizes_1t), (cores, sizes_mt)):
+        oracle.set_threads(threads)
+        for A in sizes:
+            prot = inputs.random_protein(A, seed0 + A)
+            w = inputs.random_codon_weights(seed0 + A)
+            t0 = time.perf_counter()
+            o = oracle.run(par, prot, w, lam)
+            dt = time.perf_counter() - t0
+            out.append({"aa": A, "threads": threads, "seconds": dt,
+                        "retained_cell_updates": o.retained_cells})
+    oracle.set_threads(1)
+    return out, cores
+
+
+def extrapolate(points, threads, target_aa=LENGTH):
+    """Power-law fit t = c * A^p through the largest two points of one thread
+    count, extrapolated to target_aa; returns (seconds, p)."""
+    pts = sorted((p["aa"], p["seconds"]) for p in points if p["threads"] == threads)
+    (a1, t1), (a2, t2) = pts[-2], pts[-1]
+    p = math.log(t2 / t1) / math.log(a2 / a1)
+    return t2 * (target_aa / a2) ** p, p
+
+
+def cpu_baseline():
+    """The oracle as it stands on a bounded sample of the workload (seeded
+    proteins of 60-240 aa at lambda = 4): single-threaded and on all host
+    cores; the 925-aa time is extrapolated with the growth rate of the two
+    largest all-core samples."""
+    pts, cores = oracle_series([60, 120], [60, 120, 240])
+    secs, p = extrapolate(pts, cores)
+    secs1, p1 = extrapolate(pts, 1)
+    return {"value": 1.0 / secs, "unit": "designs/s", "cores": cores, "kind": "oracle",
+            "sample": f"one protein each of 60/120 aa on 1 thread and 60/120/240 aa on all "
+                      f"{cores} cores (each span's layer pairs in parallel), lambda=4; the "
+                      f"925-aa time extrapolated as t ~ A^{p:.2f} from the two largest all-core "
+                      f"samples",
+            "points": pts, "growth_exponent": p, "single_thread_designs_per_s": 1.0 / secs1,
+            "single_thread_growth_exponent": p1}
 
 
 def run_reference(args):
-    """The oracle timed as the reference arm (rank 0 only)."""
+    """The oracle timed as the reference arm (rank 0 only): each step times a
+    bounded sample (one 60-aa and one 120-aa protein on all host cores) and
+    extrapolates its 925-aa design time with the sample's growth rate."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import oracle
-    from paper_2609_32308_b300 import inputs
-    par = energy_path()
-    oracle.build()
-    # cell updates of one 925-aa design, counted by the oracle's own definition
-    # on the sample and scaled by layer pairs (n^2) -- no GPU on this arm
-    sample = args.cpu_sample_aa
-    times, cells = [], []
+    small = max(10, args.cpu_sample_aa // 2)
+    big = max(small + 5, args.cpu_sample_aa)
+    times, rates = [], []
     for step in range(args.warmup + args.steps):
-        prot = inputs.random_protein(sample, 500000 + step)
-        w = inputs.random_codon_weights(500000 + step)
         t0 = time.perf_counter()
-        o = oracle.run(par, prot, w, LAMBDA)
+        pts, cores = oracle_series([], [small, big], seed0=500000 + step)
         dt = time.perf_counter() - t0
+        secs, p = extrapolate(pts, cores)
         if step >= args.warmup:
             times.append(dt)
-            cells.append(o.retained_cells)
-    rate = sum(cells) / sum(times)
-    scale = (3 * LENGTH) ** 2 / (3 * sample) ** 2
-    per_design = statistics.mean(cells) * scale
-    value = rate / per_design
+            rates.append(1.0 / secs)
+    value = statistics.mean(rates)
     line = {"metric": METRIC, "value": value, "unit": "designs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{LENGTH} aa (2,775 nt) lambda=4, oracle on a "
-                                   f"{sample}-aa sample per step", "length_aa": LENGTH,
+            "config": {"workload": f"{LENGTH} aa (2,775 nt) lambda=4, dense CPU oracle on a "
+                                   f"{small}- and a {big}-aa sample per step", "length_aa": LENGTH,
                        "lambda": LAMBDA},
-            "cpu_baseline": {"value": value, "unit": "designs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"one {sample}-aa protein per step; cell-update rate "
-                                       f"scaled to a 925-aa design by (n/n_sample)^2"},
+            "cpu_baseline": {"value": value, "unit": "designs/s", "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"one {small}-aa and one {big}-aa protein per step on all "
+                                       f"{cores} cores; 925-aa time extrapolated with their "
+                                       f"growth exponent"},
             "e2e": {"value": value, "unit": "designs/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0},
-            "retained_cell_updates_per_s": rate}
+                    "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def run_once(args):
-    """One untimed pass of the batched plan (fixed launch order: clear, one fill
-    launch per span, exterior, traceback) for a profiler to capture."""
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def timed_runs(plan, stream, steps):
+    """Device time of `steps` runs of a plan on `stream` (CUDA events)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        plan.run(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / 1000.0
+
+
+def measured_alu_peaks():
+    import ctypes
     import paper_2609_32308_b300 as sd
-    E = sd.sd_load_energy(energy_path())
-    prots, ws, lams = workload(args.batch, 0, args.length)
+    out = {}
+    for bits in (32, 64):
+        r = ctypes.c_double()
+        rc = sd.lib().sd_peak_addmin(bits, 2000, ctypes.byref(r))
+        if rc != 0:
+            raise sd.SdError(rc, "sd_peak_addmin")
+        out[bits] = r.value
+    return out
+
+
+def extras(sd, E, stream, pred, args):
+    """Workloads of the measurement plan beyond the headline (untimed by the
+    headline; each is timed on its own with CUDA events)."""
+    import numpy as np
+    from paper_2609_32308_b300 import inputs
+    out = {}
+    # 925 aa at lambda = 0 (one design)
+    prots, ws, lams = workload(1, 0, LENGTH, 0.0)
     plan = sd.Plan(E, prots, ws, lams)
-    plan.group = args.group
-    plan.run()
-    res = plan.results()
-    assert all(r["status"] == 0 for r in res)
-    print(json.dumps({"once": True, "batch": args.batch, "length_aa": args.length,
-                      "group": args.group, "energy0": res[0]["energy"],
-                      "device_gb": plan.device_bytes / 1e9}), flush=True)
+    plan.set_timing(True)
+    plan.run(stream)
+    r = plan.results()[0]
+    ms = plan.phase_times()
+    n = 3 * LENGTH
+    out["925aa_lambda0"] = {"fill_ms": ms[0], "total_ms": sum(ms), "energy_dcal": r["energy"],
+                            "Z": r["Z"], "Z_over_n2": r["Z"] / n ** 2,
+                            "Z_over_B_finite": r["Z"] / max(1, r["finite_direct"])}
     plan.free()
+    # 1,976 aa at lambda = 4: device footprint and retained-cell density
+    A = 1976
+    prot = inputs.random_protein(A, 1976)
+    w = inputs.random_codon_weights(1976)
+    plan = sd.Plan(E, [prot], w[None, :], [LAMBDA])
+    plan.set_timing(True)
+    plan.run(stream)
+    r = plan.results()[0]
+    ms = plan.phase_times()
+    n = 3 * A
+    pairs = n * (n + 1) // 2
+    out["1976aa_lambda4"] = {"device_bytes": plan.device_bytes, "fill_ms": ms[0],
+                             "total_ms": sum(ms), "retained_cells": r["retained_cells"],
+                             "layer_pairs": pairs,
+                             "retained_cells_per_layer_pair": r["retained_cells"] / pairs,
+                             "Z": r["Z"], "Z_over_n2": r["Z"] / n ** 2,
+                             "status": r["status"]}
+    plan.free()
+    # batch-size sweep at 925 aa, lambda = 4 (fill group 8, presized, graph)
+    sweep = {}
+    for B in [int(x) for x in args.sweep.split(",") if x]:
+        prots, ws, lams = workload(B, 0)
+        plan = sd.Plan(E, prots, ws, lams, predictor=pred, margin=2.0)
+        plan.group = 8
+        plan.set_graph(True)
+        plan.run(stream)
+        res = plan.results()
+        dt = timed_runs(plan, stream, 1)
+        sweep[str(B)] = {"designs_per_s": B / dt, "s_per_step": dt,
+                         "device_gb": plan.device_bytes / 1e9,
+                         "ok": all(x["status"] == 0 for x in res)}
+        plan.free()
+    out["batch_sweep_925aa_lambda4"] = sweep
+    return out
 
 
 def main():
@@ -273,11 +364,7 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.once:
-        run_once(args)
-        return
     import torch
-    import numpy as np
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -295,14 +382,14 @@ def main():
     def ranks_max(x: float) -> float:
         return max_over_ranks(x, dist, "cuda")
 
-    E = sd.sd_load_energy(energy_path())
+    E = load_energy()
     prots, ws, lams = workload(args.batch, rank)
     stream = torch.cuda.current_stream()
+    peaks = measured_alu_peaks()              # before any timed work
 
     # ---------------- batched: inputs resident in HBM ----------------
-    # launch order (fixed, so that a profiler can skip straight to the timed
-    # step): W warm-up steps (the first three are the autotuner's runs, one per
-    # group size), then K timed steps, each n + 3 launches (one graph replay)
+    # launch order: W warm-up steps (the first three are the autotuner's runs,
+    # one per group size), then K timed steps, each one graph replay
     pred = None
     if not args.no_predictor:
         from paper_2609_32308_b300 import retention
@@ -341,13 +428,13 @@ def main():
     room, room_worst = plan.candidate_room, plan.candidate_room_worst
     dense_ctl = None
     if args.dense_control:
-        # outside the timed region: same plan, same kernels, dense retention
-        # (presized lists overflow and are regrown to worst-case room first)
+        # same plan, same kernels, dense retention (presized lists overflow
+        # and are regrown to worst-case room first)
         z_sparse = sum(r["Z"] for r in res)
         plan.set_graph(False)
         plan.set_dense(True)
         plan.run(stream)
-        dres = plan.results()
+        plan.results()
         plan.run(stream)
         dfill = plan.phase_times()[0]
         dres = plan.results()
@@ -365,23 +452,23 @@ def main():
     device_bytes = plan.device_bytes
     group = plan.group
     ops = int(plan.count_ops().sum())          # algorithmic INT32 slots of one fill
+    fill_launches = max(r["n"] for r in res)
+    layer_pairs = sum(r["n"] * (r["n"] + 1) // 2 for r in res)
     plan.free()
 
-    # ---------------- plain: one design per launch sequence ----------------
+    # ------- plain: one design per launch sequence, its own tuned group -------
     plain = sd.Plan(E, prots[:1], ws[:1], lams[:1])
+    plain_tune = plain.autotune()
     for _ in range(max(1, args.warmup)):
         plain.run(stream)
-    torch.cuda.synchronize()
     barrier()
-    p0 = torch.cuda.Event(enable_timing=True)
-    p1 = torch.cuda.Event(enable_timing=True)
-    p0.record(stream)
-    for _ in range(args.steps):
-        plain.run(stream)
-    p1.record(stream)
-    torch.cuda.synchronize()
-    plain_elapsed = ranks_max(p0.elapsed_time(p1) / 1000.0)
+    plain_elapsed = ranks_max(timed_runs(plain, stream, args.steps))
     plain_value = world * args.steps / plain_elapsed
+    plain_group = plain.group
+    # the same single design at the batch's fill group
+    plain.group = group
+    plain.run(stream)
+    plain_at_batch_group = args.steps / timed_runs(plain, stream, args.steps)
     plain.free()
 
     # ---------------- end to end through the C ABI, host buffers ----------
@@ -403,23 +490,39 @@ def main():
            "note": "sd_design_batch per step: validation, DFA build, device tables, fill, "
                    "exterior, traceback, result copies (pageable host buffers)"}
 
+    extra = None
+    if not args.no_extras and rank == 0:
+        extra = extras(sd, E, stream, pred, args)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    pk, src = peaks()
-    max_mhz = float(pk.get("sm_max_mhz", 2032.0))
+    pk, src = peaks_file()
     fill_s = phase[0] / 1000.0
     achieved = ops / fill_s / 1e12
-    peak = alu_peak_tops(max_mhz)
+    peak = peaks[32] / 1e12
+    sha = kernel_sha()
+    traffic = None
+    if FILL_DRAM["sha256"] and sha == FILL_DRAM["sha256"]:
+        traffic = FILL_DRAM["bytes_per_layer_pair"] * layer_pairs / fill_launches
     roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": fill_traffic(),
+            "frac": achieved / peak, "traffic": traffic,
             "kernel": "k_fill_span",
-            "work": f"{ops} algorithmic INT32 slots per fill of the batch (counted: every "
-                    f"min-plus term with finite operands = 2 x (int64 adds + 1 min)), "
-                    f"{plan_launch_count(res)} fill launches per step",
-            "peak_source": f"derived issue-width peak: {SMS} SMs x {LANES_PER_SM} lanes x "
-                           f"{max_mhz:.0f} MHz ({src} max clock)",
+            "work": f"{ops} algorithmic INT32 slots per fill of the batch (counted by the "
+                    f"counting variant of the fill: every min-plus term with finite operands "
+                    f"= 2 x (int64 additions + 1 min)), {fill_launches} fill launches per step",
+            "peak_source": "measured on this GPU by sd_peak_addmin: independent chains of "
+                           "x = min(x + s, t) in int32, add and min counted as one op each",
+            "int64_view": {"achieved_tops": ops / 2 / fill_s / 1e12,
+                           "peak_tops": peaks[64] / 1e12,
+                           "frac": (ops / 2 / fill_s) / peaks[64],
+                           "int32_slots_per_int64_op": peaks[32] / peaks[64],
+                           "note": "the same work counted in int64 adds and mins against "
+                                   "the measured int64 add/min rate"},
+            "traffic_note": "dram bytes per layer pair from a one-launch small-case capture of "
+                            "this kernel source, times the bench's layer pairs per launch"
+                            if traffic is not None else "no capture of this kernel source",
             "fill_ms_per_step": phase[0]}
     line = {"metric": METRIC, "value": value, "unit": "designs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * elapsed / args.steps,
@@ -436,20 +539,23 @@ def main():
                              f"{device_bytes / 1e9:.1f} GB per batch)"},
             "retained_cell_updates_per_s": cell_rate,
             "plain_designs_per_s": plain_value,
+            "plain_fill_group": plain_group,
+            "plain_autotune_fill_ms": plain_tune,
+            "plain_designs_per_s_at_batch_group": plain_at_batch_group,
             "batched_over_plain": value / plain_value,
             "phase_ms": {"fill": phase[0], "exterior": phase[1], "traceback": phase[2]},
+            "measured_alu_peaks_tops": {"int32_addmin": peaks[32] / 1e12,
+                                        "int64_addmin": peaks[64] / 1e12},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
     if dense_ctl is not None:
         line["dense_control"] = dense_ctl
+    if extra is not None:
+        line["extras"] = extra
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_aa, cells / args.batch)
+        line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
-
-
-def plan_launch_count(res) -> int:
-    return max(r["n"] for r in res) if res else 0
 
 
 if __name__ == "__main__":

@@ -35,8 +35,8 @@ def build(force: bool = False) -> str:
     """Compile liboracle.so next to its source (plain gcc, no GPU)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-Wall", "-shared",
-                               "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-Wall", "-fopenmp",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -68,6 +68,8 @@ def _load():
         lib.orc_hairpin_energy.restype = ctypes.c_int
         lib.orc_twoloop_energy.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p]
         lib.orc_twoloop_energy.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -156,6 +158,13 @@ def run_rna(param_path: str, rna: str) -> OracleDesign:
         return OracleDesign(h, st)
     finally:
         lib.orc_free(h)
+
+
+def set_threads(n: int) -> int:
+    """Threads filling the layer pairs of one span (the paper's scheme of
+    parallelising each span over its layer pairs); 1 by default.  Returns the
+    previous setting.  Results do not depend on it."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def codon_cost_fx(lam: float, w: float) -> int:

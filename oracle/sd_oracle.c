@@ -595,6 +595,8 @@ static int64_t closed_value(const orc_design *D, int a, int b, int t) {
   return best;
 }
 
+static int g_threads = 1; /* threads filling one span (orc_set_threads) */
+
 static void fill(orc_design *D) {
   OLattice *L = &D->L;
   int N = L->N, n = L->n;
@@ -610,7 +612,10 @@ static void fill(orc_design *D) {
   for (size_t k = 0; k < NN; k++) { D->H[k] = D->Bv[k] = D->D1[k] = D->D2[k] = D->PD[k] = ORC_INF; }
   for (size_t k = 0; k < NN * 6; k++) D->V[k] = ORC_INF;
   for (int g = 1; g <= n; g++)
-    for (int i = 0; i + g <= n; i++) {
+    /* the cells of one span depend only on smaller spans (Algorithm 1), so
+       its layer pairs may be filled by several threads (one by default) */
+#pragma omp parallel for schedule(dynamic, 1) num_threads(g_threads)
+    for (int i = 0; i <= n - g; i++) {
       int j = i + g;
       for (int a = L->lstart[i]; a < L->lstart[i + 1]; a++)
         for (int b = L->lstart[j]; b < L->lstart[j + 1]; b++) {
@@ -1107,4 +1112,12 @@ int orc_twoloop_energy(const char *param_path, const char *left, const char *rig
               : twoloop_energy(P, t, ti, l1, l2, a[1], a[nl - 2], b[1], b[nr - 2]);
   free(P);
   return e;
+}
+
+/* threads used to fill the layer pairs of one span (default 1); returns the
+ * previous setting */
+int orc_set_threads(int n) {
+  int old = g_threads;
+  g_threads = n > 0 ? n : 1;
+  return old;
 }

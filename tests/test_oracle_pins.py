@@ -396,3 +396,19 @@ def test_oracle_reproduces_its_golden_designs(par1):
         w = inputs.random_codon_weights(int(seed))
         o = oracle.run(par1, prot, w, float(lam))
         assert (o.mrna, o.structure, o.energy, o.obj_fx, o.Z) == (mrna, st, int(e), int(ofx), int(Z))
+
+
+def test_oracle_threads_do_not_change_tables(par1):
+    """Filling each span's layer pairs on several threads (the paper's scheme,
+    Algorithm 1) gives the same tables and design as one thread."""
+    prot = inputs.random_protein(40, 77)
+    w = inputs.random_codon_weights(77)
+    a = oracle.run(par1, prot, w, 4.0)
+    old = oracle.set_threads(4)
+    try:
+        b = oracle.run(par1, prot, w, 4.0)
+    finally:
+        oracle.set_threads(old)
+    assert (a.mrna, a.structure, a.obj_fx) == (b.mrna, b.structure, b.obj_fx)
+    for name in ("H", "V", "B", "D1", "D2", "PD", "Ext", "cand"):
+        assert np.array_equal(getattr(a, name), getattr(b, name)), name
