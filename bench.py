@@ -356,6 +356,37 @@ def extras(sd, E, stream, pred, args):
                          "ok": all(x["status"] == 0 for x in res)}
         plan.free()
     out["batch_sweep_925aa_lambda4"] = sweep
+    # mixed lengths: log-uniform 50-1,000 aa, lambda in {0, 4} with p = 1/2,
+    # per-protein weights; one graph-captured launch sequence vs the predicted
+    # schedule (designs over 4 streams, longest predicted work first)
+    if args.mixed > 0:
+        lengths = inputs.lengths_log_uniform(args.mixed, 50, 1000, seed=4)
+        batch = inputs.protein_batch(lengths, seed=4)
+        prots = [b[0] for b in batch]
+        ws = np.stack([b[1] for b in batch])
+        lams = [b[2] for b in batch]
+        t_build = time.perf_counter()
+        plan = sd.Plan(E, prots, ws, lams, predictor=pred, margin=2.0)
+        t_build = time.perf_counter() - t_build
+        plan.group = 8
+        mixed = {"proteins": len(prots), "aa_total": sum(lengths), "max_aa": max(lengths),
+                 "device_gb": plan.device_bytes / 1e9, "plan_create_s": t_build}
+        ref = None
+        for k in (1, 4):
+            plan.streams = k
+            plan.set_graph(True)
+            plan.run(stream)
+            res = plan.results()
+            dt = timed_runs(plan, stream, 1)
+            sig = [(r["status"], r["objective_fx"], r["mrna"]) for r in plan.results()]
+            ref = sig if ref is None else ref
+            mixed[f"streams{k}"] = {"designs_per_s": len(prots) / dt, "s_per_step": dt,
+                                    "same_designs": sig == ref,
+                                    "regrows": sum(r["regrows"] for r in res)}
+        mixed["predicted_over_single_stream"] = (mixed["streams4"]["designs_per_s"] /
+                                                 mixed["streams1"]["designs_per_s"])
+        plan.free()
+        out["mixed_512_log_uniform_50_1000aa"] = mixed
     return out
 
 

@@ -170,6 +170,21 @@ int sd_plan_autotune(sd_plan *plan, float *ms3);
  * (re-captured when the group size or timing changes).  Off by default. */
 int sd_plan_set_graph(sd_plan *plan, int enable);
 
+/* Multi-stream schedule (not in the paper; it only orders work): split the
+ * plan's designs over k concurrent CUDA streams (1 <= k <= 16), assigned
+ * longest-processing-time first by predicted fill work -- each design's layer
+ * pairs, plus, when the plan was presized by the retention predictor, its
+ * predicted multiloop candidate visits (sd_plan_create_predicted).  Every
+ * stream runs the span wavefront of its own designs, so the late spans of one
+ * stream, too small to fill the GPU, overlap with the others.  A run forks
+ * from the caller's stream and joins back into it, also inside a captured
+ * graph.  Results do not depend on k.  With k > 1 sd_plan_phase_times gives
+ * (whole run, 0, 0).  k = 1 restores one launch sequence.  Synchronous: waits
+ * for the plan's last run.  Returns SD_OK, SD_EINVAL (NULL plan, k out of
+ * range) or SD_ECUDA; sd_plan_get_streams returns the current k. */
+int sd_plan_set_streams(sd_plan *plan, int k);
+int sd_plan_get_streams(const sd_plan *plan);
+
 /* Number of kernel launches one sd_plan_run enqueues. */
 int64_t sd_plan_launches(const sd_plan *plan);
 

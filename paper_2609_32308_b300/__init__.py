@@ -77,6 +77,9 @@ def lib():
         L.sd_plan_count_ops.argtypes = [P, P]
         L.sd_plan_set_group.argtypes = [P, I]
         L.sd_plan_set_graph.argtypes = [P, I]
+        L.sd_plan_set_streams.argtypes = [P, I]
+        L.sd_plan_get_streams.argtypes = [P]
+        L.sd_peak_addmin.argtypes = [I, I, ctypes.POINTER(D)]
         L.sd_plan_retention.argtypes = [P, I, P]
         L.sd_plan_candidate_room.argtypes = [P]
         L.sd_plan_candidate_room.restype = ctypes.c_int64
@@ -106,6 +109,7 @@ def lib():
                   "sd_plan_edges", "sd_plan_set_timing", "sd_plan_phase_times",
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
                   "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention", "sd_plan_set_dense",
+                  "sd_plan_set_streams", "sd_plan_get_streams", "sd_peak_addmin",
                   "sd_plan_create_predicted", "sd_pred_create", "sd_pred_get_params",
                   "sd_pred_set_params", "sd_pred_features", "sd_pred_forward",
                   "sd_pred_gradients", "sd_pred_train_step"):
@@ -271,6 +275,17 @@ class Plan:
         rc = lib().sd_plan_set_graph(self.handle, int(bool(enable)))
         if rc != SD_OK:
             raise SdError(rc, "sd_plan_set_graph")
+
+    @property
+    def streams(self) -> int:
+        return int(lib().sd_plan_get_streams(self.handle))
+
+    @streams.setter
+    def streams(self, k: int):
+        """Split the designs over k concurrent streams, LPT by predicted work."""
+        rc = lib().sd_plan_set_streams(self.handle, int(k))
+        if rc != SD_OK:
+            raise SdError(rc, "sd_plan_set_streams")
 
     def autotune(self):
         """Pick the fastest group size; returns {group: fill ms}."""

@@ -360,6 +360,18 @@ struct PlanItem {
   SdDesign d{};        // device pointers (host copy of the struct)
   int regrows = 0;     // runs repeated because a presized candidate list overflowed
   int32_t *own_cand = nullptr;  // worst-case candidate room allocated by a regrow
+  double pred_visits = -1.0;    // predicted candidate visits of the S2 scans (< 0: none)
+};
+
+// Designs of a plan that run on one stream of a multi-stream schedule.
+struct PlanBin {
+  std::vector<int> dev;           // device indices of the plan, non-increasing n
+  std::vector<int> ns;
+  std::vector<int32_t> cpre;
+  SdDesign *d_designs = nullptr;  // copies of the plan's records, in bin order
+  int32_t *d_cpre = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t done = nullptr;
 };
 
 struct sd_plan {
@@ -385,6 +397,9 @@ struct sd_plan {
   bool timing = false;
   bool timed_run = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // multi-stream schedule (sd_plan_set_streams): bins run concurrently
+  std::vector<PlanBin> bins;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -538,6 +553,17 @@ int presize(sd_predictor *pred, double margin, std::vector<PlanItem> &items) {
     for (int k = 0; k < A; k++)
       for (int s = 0; s < 8; s++)
         total[k] += std::expm1(std::max(0.f, y[((size_t)b * Lmax + k) * 8 + s]));
+    // predicted S2-scan visits: a candidate c of a list ending at codon k
+    // in span band s is visited once per start state before it, about
+    // 3k - (typical span of band s) layers
+    double visits = 0.0;
+    for (int k = 0; k < A; k++)
+      for (int s = 0; s < 8; s++) {
+        const double span = s == 7 ? 768.0 : 6.0 * std::ldexp(1.0, s);
+        visits += std::expm1(std::max(0.f, y[((size_t)b * Lmax + k) * 8 + s])) *
+                  std::max(0.0, 3.0 * k - span);
+      }
+    items[idx[b]].pred_visits = visits;
     L.caps.assign(L.N, 0);
     for (int v = 0; v < L.N; v++) {
       if (L.layer[v] < 1) continue;
@@ -648,13 +674,74 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
 }
 }  // namespace
 
+namespace {
+// An event record that is also an event-record node of a graph being captured
+// on the stream (a plain record there is only a capture dependency).
+void record_timing(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, st);
+}
+
+// Enqueue one whole run on `st`: one launch sequence over all designs, or,
+// with a multi-stream schedule, one per bin on the bins' streams, forked
+// from and joined back into `st` (the same pattern is captured into graphs).
+int enqueue(sd_plan *p, cudaStream_t st, int64_t *nl) {
+  void *ev[4] = {p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
+  if (p->bins.empty())
+    return sd_k_run(p->d_designs, (int)p->hdesigns.size(), p->ns.data(), p->d_cpre,
+                    p->energy->d, st, nl, p->timing ? ev : nullptr, p->group);
+  if (p->timing) record_timing(p->ev[0], st);
+  if (cudaEventRecord(p->fork, st) != cudaSuccess) return -1;
+  int64_t total = 0;
+  for (auto &b : p->bins) {
+    int64_t n1 = 0;
+    if (cudaStreamWaitEvent(b.st, p->fork, 0) != cudaSuccess) return -1;
+    if (sd_k_run(b.d_designs, (int)b.dev.size(), b.ns.data(), b.d_cpre, p->energy->d, b.st, &n1,
+                 nullptr, p->group))
+      return -1;
+    total += n1;
+    if (cudaEventRecord(b.done, b.st) != cudaSuccess ||
+        cudaStreamWaitEvent(st, b.done, 0) != cudaSuccess)
+      return -1;
+  }
+  if (p->timing)
+    for (int k = 1; k < 4; k++) record_timing(p->ev[k], st);
+  *nl = total;
+  return 0;
+}
+
+// Upload the bins' copies of the design records (after a regrow or a
+// change of retention rule touched the plan's records).
+int refresh_bins(sd_plan *p) {
+  for (auto &b : p->bins) {
+    std::vector<SdDesign> h;
+    for (int d : b.dev) h.push_back(p->hdesigns[d]);
+    if (cudaMemcpy(b.d_designs, h.data(), sizeof(SdDesign) * h.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return SD_ECUDA;
+  }
+  return SD_OK;
+}
+
+void free_bins(sd_plan *p) {
+  for (auto &b : p->bins) {
+    if (b.d_designs) cudaFree(b.d_designs);
+    if (b.d_cpre) cudaFree(b.d_cpre);
+    if (b.st) cudaStreamDestroy(b.st);
+    if (b.done) cudaEventDestroy(b.done);
+  }
+  p->bins.clear();
+}
+}  // namespace
+
 extern "C" int sd_plan_run(sd_plan *p, void *stream) {
   if (!p) return SD_EINVAL;
   p->last_stream = (cudaStream_t)stream;
   if (p->hdesigns.empty()) return SD_OK;
   int64_t nl = 0;
-  void *ev[4] = {p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
-  const int nd = (int)p->hdesigns.size();
   if (p->use_graph) {
     if (p->gexec && p->graph_timed != p->timing) {
       cudaGraphExecDestroy(p->gexec);
@@ -667,8 +754,7 @@ extern "C" int sd_plan_run(sd_plan *p, void *stream) {
       cudaGraph_t graph = nullptr;
       if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
         return SD_ECUDA;
-      int rc = sd_k_run(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, p->cap_stream,
-                        &nl, p->timing ? ev : nullptr, p->group);
+      int rc = enqueue(p, p->cap_stream, &nl);
       cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &graph);
       if (rc != 0 || ce != cudaSuccess || !graph) {
         if (graph) cudaGraphDestroy(graph);
@@ -688,11 +774,83 @@ extern "C" int sd_plan_run(sd_plan *p, void *stream) {
     p->timed_run = p->timing;
     return cudaGraphLaunch(p->gexec, (cudaStream_t)stream) == cudaSuccess ? SD_OK : SD_ECUDA;
   }
-  int rc = sd_k_run(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, stream, &nl,
-                    p->timing ? ev : nullptr, p->group);
+  int rc = enqueue(p, (cudaStream_t)stream, &nl);
   p->launches = nl;
   p->timed_run = p->timing;
   return rc == 0 ? SD_OK : SD_ECUDA;
+}
+
+// Predicted fill work of one design in candidate-visit units: the closed and
+// two-loop cells cost about the same per layer pair (a few hundred min-plus
+// terms, kLayerPairWork), the multiloop splits one visit per retained
+// candidate and start state (predicted by the retention predictor when the
+// plan has one, else taken as zero).
+static double design_work(const PlanItem &it) {
+  constexpr double kLayerPairWork = 300.0;
+  const double n = it.L.n;
+  return kLayerPairWork * n * (n + 1) / 2 + std::max(0.0, it.pred_visits);
+}
+
+extern "C" int sd_plan_set_streams(sd_plan *p, int k) {
+  if (!p || k < 1 || k > 16) return SD_EINVAL;
+  if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return SD_ECUDA;
+  if (p->gexec) {
+    cudaGraphExecDestroy(p->gexec);
+    p->gexec = nullptr;
+  }
+  free_bins(p);
+  const int nd = (int)p->hdesigns.size();
+  if (k == 1 || nd < 2) return SD_OK;
+  k = std::min(k, nd);
+  // longest processing time first: heaviest design to the lightest bin
+  std::vector<int> item_of(nd, -1);
+  for (size_t q = 0; q < p->items.size(); q++)
+    if (p->items[q].dev_index >= 0) item_of[p->items[q].dev_index] = (int)q;
+  std::vector<int> order(nd);
+  std::vector<double> w(nd);
+  for (int d = 0; d < nd; d++) {
+    order[d] = d;
+    w[d] = design_work(p->items[item_of[d]]);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+  std::vector<double> load(k, 0.0);
+  p->bins.resize(k);
+  for (int d : order) {
+    const int b = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[b] += w[d];
+    p->bins[b].dev.push_back(d);
+  }
+  int rc = SD_OK;
+  if (!p->fork && cudaEventCreateWithFlags(&p->fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = SD_ECUDA;
+  for (auto &b : p->bins) {
+    if (rc != SD_OK) break;
+    // the span work queue needs each bin's designs longest first
+    std::stable_sort(b.dev.begin(), b.dev.end(),
+                     [&](int x, int y) { return p->ns[x] > p->ns[y]; });
+    b.cpre.assign(1, 0);
+    for (int d : b.dev) {
+      b.ns.push_back(p->ns[d]);
+      b.cpre.push_back(b.cpre.back() + p->ns[d] + 1);
+    }
+    if (cudaStreamCreateWithFlags(&b.st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(&b.d_designs, sizeof(SdDesign) * b.dev.size()) != cudaSuccess ||
+        cudaMalloc(&b.d_cpre, sizeof(int32_t) * b.cpre.size()) != cudaSuccess ||
+        cudaMemcpy(b.d_cpre, b.cpre.data(), sizeof(int32_t) * b.cpre.size(),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+      rc = SD_ECUDA;
+  }
+  if (rc == SD_OK) rc = refresh_bins(p);
+  if (rc != SD_OK) {
+    cudaGetLastError();
+    free_bins(p);
+  }
+  return rc;
+}
+
+extern "C" int sd_plan_get_streams(const sd_plan *p) {
+  return p ? std::max<int>(1, (int)p->bins.size()) : SD_EINVAL;
 }
 
 extern "C" int sd_plan_set_graph(sd_plan *p, int enable) {
@@ -846,7 +1004,8 @@ int regrow_if_needed(sd_plan *p) {
     cpre.push_back(cpre.back() + it.L.n + 1);
   }
   if (cudaMemcpy(p->d_designs, p->hdesigns.data(), sizeof(SdDesign) * p->hdesigns.size(),
-                 cudaMemcpyHostToDevice) != cudaSuccess)
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      refresh_bins(p) != SD_OK)
     return SD_ECUDA;
   SdDesign *d_sub = nullptr;
   int32_t *d_cpre = nullptr;
@@ -971,7 +1130,7 @@ extern "C" int sd_plan_set_dense(sd_plan *p, int enable) {
       cudaMemcpy(p->d_designs, p->hdesigns.data(), sizeof(SdDesign) * p->hdesigns.size(),
                  cudaMemcpyHostToDevice) != cudaSuccess)
     return SD_ECUDA;
-  return SD_OK;
+  return refresh_bins(p);
 }
 
 extern "C" int64_t sd_plan_candidate_room_worst(const sd_plan *p) {
@@ -1079,6 +1238,8 @@ extern "C" void sd_plan_free(sd_plan *p) {
   for (auto &it : p->items)
     if (it.own_cand) cudaFree(it.own_cand);
   if (p->gexec) cudaGraphExecDestroy(p->gexec);
+  free_bins(p);
+  if (p->fork) cudaEventDestroy(p->fork);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   for (int k = 0; k < 4; k++)
     if (p->ev[k]) cudaEventDestroy(p->ev[k]);

@@ -41,6 +41,21 @@ __constant__ int c_pair3[6] = {3, 2, 1, 0, 3, 2};
 __constant__ int c_rev[6] = {3, 2, 1, 0, 5, 4};
 
 __device__ __forceinline__ int64_t fx(int e) { return (int64_t)e * 4294967296LL; }
+
+// Reads of cells filled by earlier launches (every span below the current
+// one) go through the read-only data path; cells of the current span (the
+// stack option's inner cell, the multiloop option's S2) are read coherently.
+#ifndef SD_NC
+#define SD_NC 1
+#endif
+template <class T>
+__device__ __forceinline__ T ro(const T *p) {
+#if SD_NC
+  return __ldg(p);
+#else
+  return *p;
+#endif
+}
 __device__ __forceinline__ bool fin(int64_t v) { return v < SD_FINLIM; }
 
 __device__ __forceinline__ int64_t diag_off(int64_t n, int64_t g) {
@@ -174,13 +189,25 @@ struct Fv {
   // min path cost, 0 on the same state, +inf on another state of the same layer
   __device__ __forceinline__ int64_t Hh(int lx, int sx, int ly, int sy) const {
     if (ly == lx) return sx == sy ? 0 : SD_INF;
-    return H[cs(lx, sx, ly, sy)];
+    return ro(H + cs(lx, sx, ly, sy));
   }
   __device__ __forceinline__ int nout(int v) const { return on[v]; }
   __device__ __forceinline__ int nin(int v) const { return in_[v]; }
   __device__ __forceinline__ SdEdge out(int v, int k) const { return oe[v * SD_MAXOUT + k]; }
   __device__ __forceinline__ SdEdge in(int v, int k) const { return ie[v * SD_MAXIN + k]; }
+  // V of a cell of an earlier span (read-only path) ...
   __device__ __forceinline__ void v6(int idx, int64_t (&vv)[6]) const {
+    const longlong2 *p = reinterpret_cast<const longlong2 *>(V + (int64_t)idx * 6);
+    const longlong2 a = ro(p), b = ro(p + 1), c = ro(p + 2);
+    vv[0] = a.x;
+    vv[1] = a.y;
+    vv[2] = b.x;
+    vv[3] = b.y;
+    vv[4] = c.x;
+    vv[5] = c.y;
+  }
+  // ... or of the current span (written by this launch)
+  __device__ __forceinline__ void v6_cur(int idx, int64_t (&vv)[6]) const {
     const longlong2 *p = reinterpret_cast<const longlong2 *>(V + (int64_t)idx * 6);
     const longlong2 a = p[0], b = p[1], c = p[2];
     vv[0] = a.x;
@@ -335,12 +362,14 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       if (l >= 2) {
         // bulge: bulge[l] + AU(t) + AU(inner); best inner type from the inner table
         const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
-        const int64_t w = D.W[(int64_t)rc * SD_WN + 48];
+        const int64_t w = ro(D.W + (int64_t)rc * SD_WN + 48);
         if (!fin(w)) continue;
         upd6<COUNT>(qv, tm, w + h + fx(T.bulge[l]), 2, ops, [&](int t) { return T.au[t]; });
       } else {
         int64_t vv[6];
-        F.v6(right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy), vv);
+        const int vc = right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy);
+        if (l == 0) F.v6_cur(vc, vv);
+        else F.v6(vc, vv);
         const int64_t e1 = h + fx(l == 1 ? T.bulge[1] : 0);
 #pragma unroll
         for (int ti = 0; ti < 6; ti++) {
@@ -368,7 +397,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int a = 0; a < nox; a++) {
           const SdEdge ec = F.out(x, a);
           const int p = ec.label, cs = ec.other - lx1s;
-          const int64_t w = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR];
+          const int64_t w = ro(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR);
           if (!fin(w)) continue;
           const int64_t base = w + ec.cost + r1.cost + e0;
           for (int b2 = 0; b2 < niy; b2++) {
@@ -436,7 +465,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int b = 0; b < niy; b++) {
           const SdEdge er = F.in(y, b);
           const int r = er.label, ds = er.other - ly1s;
-          const int64_t wv = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r];
+          const int64_t wv = ro(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r);
           if (!fin(wv)) continue;
           const int64_t base = wv + er.cost + p2.cost + e0;
           for (int a = 0; a < nox; a++) {
@@ -492,7 +521,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
           continue;
       } else {
-        wv = D.W[(int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR];
+        wv = ro(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR);
         if (!fin(wv)) continue;
       }
       for (int a = 0; a < nox; a++) {
@@ -528,7 +557,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int a = k / niy, b = k - a * niy;
       const SdEdge e1 = F.out(x, a), e2 = F.in(y, b);
       const int r = F.rs(lx + 1, e1.other - lx1s, ly - 1, e2.other - ly1s);
-      const int64_t il = D.IL[r];
+      const int64_t il = ro(D.IL + r);
       if (!fin(il)) continue;
       const int idx = e1.label * 4 + e2.label;
       upd6<COUNT>(qv, tm, il + e1.cost + e2.cost, 3, ops, [&](int t) { return T.mmI[t][idx]; });
@@ -654,8 +683,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       const int l = q >> 2, c = (q >> 1) & 1, sn = q & 1;
       int64_t vl = SD_INF, vr = SD_INF;
       if (active && l <= lmax) {
-        if (sn < wa && c < F.w(i + l)) vl = l == 0 ? (c == sn ? 0 : SD_INF) : F.H[F.cs(i, sn, i + l, c)];
-        if (sn < wb && c < F.w(j - l)) vr = l == 0 ? (c == sn ? 0 : SD_INF) : F.H[F.cs(j - l, c, j, sn)];
+        if (sn < wa && c < F.w(i + l)) vl = l == 0 ? (c == sn ? 0 : SD_INF) : ro(F.H + F.cs(i, sn, i + l, c));
+        if (sn < wb && c < F.w(j - l)) vr = l == 0 ? (c == sn ? 0 : SD_INF) : ro(F.H + F.cs(j - l, c, j, sn));
       }
       GS.hl[l][c * 2 + sn] = vl;
       GS.hr[l][c * 2 + sn] = vr;
@@ -682,7 +711,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       for (int k = 0; k < SD_MAXIN; k++) {
         if (k >= nib) break;
         const SdEdge e = F.in(b, k);
-        const int64_t hp = g == 1 ? (e.other == a ? 0 : SD_INF) : F.H[F.cs(i, sa, j - 1, e.other - js)];
+        const int64_t hp = g == 1 ? (e.other == a ? 0 : SD_INF) : ro(F.H + F.cs(i, sa, j - 1, e.other - js));
         if (!fin(hp)) continue;
         upd(hv, hp + e.cost);
         TERM(1);
@@ -699,7 +728,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           const SdEdge e1 = F.out(a, k1), e2 = F.in(b, k2);
           const int cs = e1.other - i1s, ds = e2.other - js;
           const int64_t w =
-              D.W[(int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label];
+              ro(D.W + (int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label);
           if (!fin(w)) continue;
           upd(iv, w + e1.cost + e2.cost);
           TERM(3);
@@ -726,7 +755,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           for (int k2 = 0; k2 < nib; k2++) {
             const SdEdge e2 = F.in(b, k2);
             if (e2.label != l3) continue;
-            const int64_t qv = D.Q[F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t];
+            const int64_t qv = ro(D.Q + F.rs(i + 1, e1.other - i1s, j - 1, e2.other - js) * 6 + t);
             if (!fin(qv)) continue;
             upd(v, qv + e1.cost + e2.cost);
             TERM(2);
@@ -787,7 +816,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           for (int ds = 0; ds < SD_W; ds++) {
             const int64_t hr0 = GS.hr[l2p][ds * 2], hr1 = GS.hr[l2p][ds * 2 + 1];
             if (!fin(hr0) && !fin(hr1)) continue;
-            const int64_t v = D.Ihat[rb + cs * SD_W + ds];
+            const int64_t v = ro(D.Ihat + rb + cs * SD_W + ds);
             if (!fin(v)) continue;
             const int64_t ve = v + e;
 #pragma unroll
@@ -823,7 +852,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       if (g >= 2 && sub == 0)
         for (int k = 0; k < F.nin(b); k++) {
           const SdEdge e = F.in(b, k);
-          const int64_t v = D.S2[F.cs(i, sa, j - 1, e.other - js)];
+          const int64_t v = ro(D.S2 + F.cs(i, sa, j - 1, e.other - js));
           if (!fin(v)) continue;
           upd(s2, v + e.cost + mlb);
           TERM(2);
@@ -834,7 +863,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         const int c = D.cand_c[off + k];
         const int lc = __ldg(&D.layer[c]);
         if (lc <= i) break;  // entries are in decreasing layer order
-        const int64_t v = D.S1[F.cs(i, sa, lc, c - F.ls(lc))];
+        const int64_t v = ro(D.S1 + F.cs(i, sa, lc, c - F.ls(lc)));
         if (!fin(v)) continue;
         upd(s2, v + D.cand_B[off + k]);
         TERM(1);
@@ -849,14 +878,14 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       if (g >= 2) {
         for (int k = 0; k < F.nout(a); k++) {
           const SdEdge e = F.out(a, k);
-          const int64_t v = D.S1[F.cs(i + 1, e.other - i1s, j, sb)];
+          const int64_t v = ro(D.S1 + F.cs(i + 1, e.other - i1s, j, sb));
           if (!fin(v)) continue;
           upd(ps, v + e.cost + mlb);
           TERM(2);
         }
         for (int k = 0; k < F.nin(b); k++) {
           const SdEdge e = F.in(b, k);
-          const int64_t v = D.S1[F.cs(i, sa, j - 1, e.other - js)];
+          const int64_t v = ro(D.S1 + F.cs(i, sa, j - 1, e.other - js));
           if (!fin(v)) continue;
           upd(ps, v + e.cost + mlb);
           TERM(2);

@@ -396,3 +396,32 @@ def test_bench_configuration_against_the_oracle(sd, E1, bench_config_batch, marg
     for k in range(len(prots)):
         compare_tables(plan, k, orc[k])
     plan.free()
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_stream_schedule_of_a_mixed_batch(sd, E1, par1, k):
+    """Designs split over k concurrent streams (longest processing time first
+    by predicted work), replayed as one graph twice, equal the oracle's; going
+    back to one stream gives the same designs."""
+    from paper_2609_32308_b300 import retention
+    lengths = [30, 7, 45, 12, 45, 3, 60, 25]
+    batch = inputs.protein_batch(lengths, seed=123)
+    prots = [b[0] for b in batch]
+    ws = np.stack([b[1] for b in batch])
+    lams = [b[2] for b in batch]
+    plan = sd.Plan(E1, prots, ws, lams, predictor=retention.load(), margin=2.0)
+    plan.streams = k
+    assert plan.streams == k
+    plan.set_graph(True)
+    plan.set_timing(True)
+    for _ in range(2):
+        plan.run()
+        res = plan.results()
+        assert plan.phase_times()[0] > 0
+        for (p, w, lam), r in zip(batch, res):
+            compare_design(r, oracle.run(par1, p, w, lam), lam)
+    plan.streams = 1
+    plan.run()
+    assert [(r["mrna"], r["objective_fx"]) for r in plan.results()] == \
+        [(r["mrna"], r["objective_fx"]) for r in res]
+    plan.free()
