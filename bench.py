@@ -222,14 +222,14 @@ def extrapolate(points, threads, target_aa=LENGTH):
 
 def cpu_baseline():
     """The oracle as it stands on a bounded sample of the workload (seeded
-    proteins of 60-240 aa at lambda = 4): single-threaded and on all host
+    proteins of 60-480 aa at lambda = 4): single-threaded and on all host
     cores; the 925-aa time is extrapolated with the growth rate of the two
     largest all-core samples."""
-    pts, cores = oracle_series([60, 120], [60, 120, 240])
+    pts, cores = oracle_series([60, 120], [120, 240, 480])
     secs, p = extrapolate(pts, cores)
     secs1, p1 = extrapolate(pts, 1)
     return {"value": 1.0 / secs, "unit": "designs/s", "cores": cores, "kind": "oracle",
-            "sample": f"one protein each of 60/120 aa on 1 thread and 60/120/240 aa on all "
+            "sample": f"one protein each of 60/120 aa on 1 thread and 120/240/480 aa on all "
                       f"{cores} cores (each span's layer pairs in parallel), lambda=4; the "
                       f"925-aa time extrapolated as t ~ A^{p:.2f} from the two largest all-core "
                       f"samples",
@@ -305,6 +305,11 @@ def measured_alu_peaks():
     return out
 
 
+def torch_sync():
+    import torch
+    torch.cuda.synchronize()
+
+
 def extras(sd, E, stream, pred, args):
     """Workloads of the measurement plan beyond the headline (untimed by the
     headline; each is timed on its own with CUDA events)."""
@@ -356,6 +361,30 @@ def extras(sd, E, stream, pred, args):
                          "ok": all(x["status"] == 0 for x in res)}
         plan.free()
     out["batch_sweep_925aa_lambda4"] = sweep
+    # one 925-aa protein at 16 values of lambda: one sweep (one batch) vs 16
+    # separate designs; and the supported envelope of a 300-aa protein
+    lam16 = [0.5 * q for q in range(16)]
+    prot = inputs.random_protein(LENGTH, 777)
+    w = inputs.random_codon_weights(777)
+    torch_sync()
+    t0 = time.perf_counter()
+    sw = sd.sd_design_sweep(E, prot, w, lam16)
+    t_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    sep = [sd.sd_design(E, prot, w, lam) for lam in lam16]
+    t_sep = time.perf_counter() - t0
+    same = [(a["mrna"], a["objective_fx"]) for a in sw] == [(b["mrna"], b["objective_fx"])
+                                                            for b in sep]
+    prot300 = inputs.random_protein(300, 778)
+    w300 = inputs.random_codon_weights(778)
+    t0 = time.perf_counter()
+    lines, breaks = sd.sd_envelope(E, prot300, w300, 0.0, 8.0)
+    t_env = time.perf_counter() - t0
+    out["lambda_sweep_925aa_16_lambdas"] = {
+        "sweep_s": t_sweep, "separate_s": t_sep, "sweep_over_separate": t_sep / t_sweep,
+        "same_designs": same}
+    out["envelope_300aa_lambda_0_8"] = {"lines": len(lines), "seconds": t_env,
+                                        "breakpoints": breaks[:8]}
     # mixed lengths: log-uniform 50-1,000 aa, lambda in {0, 4} with p = 1/2,
     # per-protein weights; one graph-captured launch sequence vs the predicted
     # schedule (designs over 4 streams, longest predicted work first)

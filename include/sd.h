@@ -106,6 +106,40 @@ int sd_design_batch(const sd_energy *energy, int count, const char *const *prote
 void sd_result_free(sd_result *r);
 const char *sd_strerror(int code);
 
+/* ---- many values of lambda for one protein (Sec. 10: supported-envelope
+ *      and inverse-lambda tools) ---- */
+
+/* Exact designs of one protein at k values of lambda (kcal/mol, >= 0), in one
+ * batched launch sequence: outs[k] and status[k] as in sd_design_batch.
+ * Returns SD_OK if the batch ran (check status[]), else an error code. */
+int sd_design_sweep(const sd_energy *energy, const char *protein, const double *codon_weights,
+                    int k, const double *lambdas, sd_result *outs, int *status);
+
+/* The supported lower envelope of F*(p, lambda) = min_r E(r) + 100 lambda C(r)
+ * over lam_lo <= lambda <= lam_hi (Eq. 1 is concave and piecewise linear in
+ * lambda; each piece is a design optimal on an interval).  lines[] receives
+ * the supported designs in order of increasing lambda (non-increasing codon
+ * cost), breaks[] (may be NULL) the count-1 lambdas where one line meets the
+ * next.  Found by exact designs at the intersections of adjacent lines, all
+ * open intersections of a round in one batch.  Lines whose values differ by
+ * less than the fixed-point rounding of the DP ((A+1) * 2^-31 dcal/mol) are
+ * one line.  lines[] is a caller array of max_lines results (free each with
+ * sd_result_free).  Returns SD_OK, SD_ESIZE (more than max_lines lines: the
+ * lines found so far are returned, *count <= max_lines, breaks between lines
+ * not yet resolved are left 0), SD_EINVAL, or the error of a design. */
+int sd_envelope(const sd_energy *energy, const char *protein, const double *codon_weights,
+                double lam_lo, double lam_hi, int max_lines, sd_result *lines, double *breaks,
+                int *count);
+
+/* The smallest lambda in [0, lam_hi] whose exact design has codon cost
+ * C(r) <= target_codon_cost (from the supported envelope on [0, lam_hi]),
+ * and that design.  Returns SD_OK, SD_EINFEASIBLE (no design of the envelope
+ * reaches the target), SD_ESIZE (more than 256 supported lines), SD_EINVAL,
+ * or the error of a design.  *out is freed with sd_result_free. */
+int sd_inverse_lambda(const sd_energy *energy, const char *protein, const double *codon_weights,
+                      double target_codon_cost, double lam_hi, double *lambda_out,
+                      sd_result *out);
+
 /* Exact design of one protein that allocates no device memory.
  * The paper has no counterpart: this entry point exists for callers that may
  * not call cudaMalloc (or an allocator built on it, such as torch's) when they

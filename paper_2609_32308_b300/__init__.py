@@ -78,6 +78,10 @@ def lib():
         L.sd_plan_set_group.argtypes = [P, I]
         L.sd_plan_set_graph.argtypes = [P, I]
         L.sd_plan_set_streams.argtypes = [P, I]
+        L.sd_design_sweep.argtypes = [P, ctypes.c_char_p, P, I, P, P, P]
+        L.sd_envelope.argtypes = [P, ctypes.c_char_p, P, D, D, I, P, P, ctypes.POINTER(I)]
+        L.sd_inverse_lambda.argtypes = [P, ctypes.c_char_p, P, D, D, ctypes.POINTER(D),
+                                        ctypes.POINTER(sd_result)]
         L.sd_plan_get_streams.argtypes = [P]
         L.sd_peak_addmin.argtypes = [I, I, ctypes.POINTER(D)]
         L.sd_plan_retention.argtypes = [P, I, P]
@@ -110,6 +114,7 @@ def lib():
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
                   "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention", "sd_plan_set_dense",
                   "sd_plan_set_streams", "sd_plan_get_streams", "sd_peak_addmin",
+                  "sd_design_sweep", "sd_envelope", "sd_inverse_lambda",
                   "sd_plan_create_predicted", "sd_pred_create", "sd_pred_get_params",
                   "sd_pred_set_params", "sd_pred_features", "sd_pred_forward",
                   "sd_pred_gradients", "sd_pred_train_step"):
@@ -219,6 +224,61 @@ def sd_design_batch(energy: Energy, proteins, weights, lambdas) -> list:
     finally:
         for k in range(count):
             lib().sd_result_free(ctypes.byref(outs[k]))
+
+
+def sd_design_sweep(energy: Energy, protein: str, weights, lambdas) -> list:
+    """Designs of one protein at several lambdas, one batched launch sequence."""
+    k = len(lambdas)
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+    lam = np.ascontiguousarray(lambdas, dtype=np.float64).reshape(k)
+    outs = (sd_result * max(k, 1))()
+    st = np.zeros(max(k, 1), dtype=np.int32)
+    rc = lib().sd_design_sweep(energy.handle, protein.encode(), _ptr(w), k, _ptr(lam), outs,
+                               _ptr(st))
+    try:
+        if rc != SD_OK:
+            raise SdError(rc, "sd_design_sweep")
+        return [_result_dict(outs[q], int(st[q])) for q in range(k)]
+    finally:
+        for q in range(k):
+            lib().sd_result_free(ctypes.byref(outs[q]))
+
+
+def sd_envelope(energy: Energy, protein: str, weights, lam_lo: float, lam_hi: float,
+                max_lines: int = 256):
+    """Supported lines of the lower envelope of F*(lambda) on [lam_lo, lam_hi]:
+    (list of design dicts in increasing lambda, list of breakpoints)."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+    lines = (sd_result * max_lines)()
+    brk = np.zeros(max_lines, dtype=np.float64)
+    cnt = ctypes.c_int()
+    rc = lib().sd_envelope(energy.handle, protein.encode(), _ptr(w), float(lam_lo),
+                           float(lam_hi), int(max_lines), lines, _ptr(brk), ctypes.byref(cnt))
+    try:
+        if rc != SD_OK:
+            raise SdError(rc, "sd_envelope")
+        n = int(cnt.value)
+        return [_result_dict(lines[q], SD_OK) for q in range(n)], [float(x) for x in brk[:n - 1]]
+    finally:
+        for q in range(int(cnt.value)):
+            lib().sd_result_free(ctypes.byref(lines[q]))
+
+
+def sd_inverse_lambda(energy: Energy, protein: str, weights, target_codon_cost: float,
+                      lam_hi: float):
+    """Smallest lambda in [0, lam_hi] whose design has C(r) <= target; (lambda, design)."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+    lam = ctypes.c_double()
+    r = sd_result()
+    rc = lib().sd_inverse_lambda(energy.handle, protein.encode(), _ptr(w),
+                                 float(target_codon_cost), float(lam_hi), ctypes.byref(lam),
+                                 ctypes.byref(r))
+    try:
+        if rc != SD_OK:
+            raise SdError(rc, "sd_inverse_lambda")
+        return float(lam.value), _result_dict(r, SD_OK)
+    finally:
+        lib().sd_result_free(ctypes.byref(r))
 
 
 class Plan:
