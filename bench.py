@@ -361,6 +361,26 @@ def extras(sd, E, stream, pred, args):
                          "ok": all(x["status"] == 0 for x in res)}
         plan.free()
     out["batch_sweep_925aa_lambda4"] = sweep
+    # table layouts (span-major slots, the paper's square arena, its
+    # forward-packed option): device bytes and fill time of one design
+    study = {}
+    for A in (925, 1976, 3677):
+        prot = inputs.random_protein(A, 9000 + A)
+        w = inputs.random_codon_weights(9000 + A)
+        row = {}
+        ref = None
+        for lay, name in ((0, "span"), (1, "square"), (2, "packed")):
+            plan = sd.Plan(E, [prot], w[None, :], [LAMBDA], layout=lay)
+            plan.set_timing(True)
+            plan.run(stream)
+            r = plan.results()[0]
+            ms = plan.phase_times()
+            ref = r["objective_fx"] if ref is None else ref
+            row[name] = {"device_gb": plan.device_bytes / 1e9, "fill_ms": ms[0],
+                         "total_ms": sum(ms), "same_optimum": r["objective_fx"] == ref}
+            plan.free()
+        study[f"{A}aa_{3 * A}nt"] = row
+    out["table_layouts_lambda4"] = study
     # one 925-aa protein at 16 values of lambda: one sweep (one batch) vs 16
     # separate designs; and the supported envelope of a 300-aa protein
     lam16 = [0.5 * q for q in range(16)]

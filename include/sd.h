@@ -171,6 +171,22 @@ int sd_plan_create(const sd_energy *energy, int count, const char *const *protei
                    const double *codon_weights, int weights_shared, const double *lambdas,
                    sd_plan **out, int *item_status);
 
+/* The same with a chosen layout of the full tables (H, V, B, S1, S2):
+ *   SD_LAYOUT_SPAN   0  layer pair (i, i+g) of span g at cell (g-1)(n+1) -
+ *                       (g-1)g/2 + i, 4 state-pair slots per cell (the default:
+ *                       the cells of one span are contiguous for the wavefront)
+ *   SD_LAYOUT_SQUARE 1  state pair (a, b) at a*N + b (Sec. 5: the square arena)
+ *   SD_LAYOUT_PACKED 2  forward-packed (Sec. 5): only pairs (a, b) with b on a
+ *                       later layer than a, row by row
+ * Results do not depend on the layout; memory and speed do (Sec. 8.2 measures
+ * packed against square on the CPU).  Anything else is SD_EINVAL. */
+#define SD_LAYOUT_SPAN 0
+#define SD_LAYOUT_SQUARE 1
+#define SD_LAYOUT_PACKED 2
+int sd_plan_create_layout(const sd_energy *energy, int count, const char *const *proteins,
+                          const double *codon_weights, int weights_shared, const double *lambdas,
+                          int layout, sd_plan **out, int *item_status);
+
 /* Run the fill, the exterior pass and the traceback of every valid item on
  * `stream` (a cudaStream_t; NULL means the legacy default stream).
  * Asynchronous: returns after enqueueing.  Re-running recomputes everything. */

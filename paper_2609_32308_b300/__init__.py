@@ -22,6 +22,7 @@ _lib = None
 
 SD_OK, SD_EINVAL, SD_ERANGE, SD_EINFEASIBLE = 0, -1, -2, -3
 SD_ENOMEM, SD_ECUDA, SD_ETIMEOUT, SD_EINTERNAL, SD_ESIZE = -4, -5, -6, -7, -8
+SD_LAYOUT_SPAN, SD_LAYOUT_SQUARE, SD_LAYOUT_PACKED = 0, 1, 2
 INF = 1 << 62          # +infinity in table dumps
 FX_ONE = 1 << 32       # one dcal/mol in the fixed-point unit
 
@@ -64,6 +65,7 @@ def lib():
         L.sd_strerror.argtypes = [I]
         L.sd_strerror.restype = ctypes.c_char_p
         L.sd_plan_create.argtypes = [P, I, P, P, I, P, ctypes.POINTER(P), P]
+        L.sd_plan_create_layout.argtypes = [P, I, P, P, I, P, I, ctypes.POINTER(P), P]
         L.sd_plan_run.argtypes = [P, P]
         L.sd_plan_launches.argtypes = [P]
         L.sd_plan_launches.restype = ctypes.c_int64
@@ -114,7 +116,7 @@ def lib():
                   "sd_plan_count_ops", "sd_plan_set_group", "sd_plan_get_group",
                   "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention", "sd_plan_set_dense",
                   "sd_plan_set_streams", "sd_plan_get_streams", "sd_peak_addmin",
-                  "sd_design_sweep", "sd_envelope", "sd_inverse_lambda",
+                  "sd_design_sweep", "sd_envelope", "sd_inverse_lambda", "sd_plan_create_layout",
                   "sd_plan_create_predicted", "sd_pred_create", "sd_pred_get_params",
                   "sd_pred_set_params", "sd_pred_features", "sd_pred_forward",
                   "sd_pred_gradients", "sd_pred_train_step"):
@@ -285,9 +287,10 @@ class Plan:
     """A batch of designs resident on the GPU (sd_plan_* calls)."""
 
     def __init__(self, energy: Energy, proteins, weights, lambdas, predictor=None,
-                 margin: float = 2.0):
+                 margin: float = 2.0, layout: int = SD_LAYOUT_SPAN):
         """predictor: a Predictor to presize the candidate lists
-        (sd_plan_create_predicted), or None for worst-case room."""
+        (sd_plan_create_predicted), or None for worst-case room.  layout: the
+        layout of the full tables (sd_plan_create_layout; worst-case room)."""
         self.energy = energy
         self.count = len(proteins)
         w, shared = _weights(weights, self.count)
@@ -296,7 +299,13 @@ class Plan:
         arr = (ctypes.c_char_p * self.count)(*self._keep)
         self.item_status = np.zeros(self.count, dtype=np.int32)
         h = ctypes.c_void_p()
-        if predictor is None:
+        if layout != SD_LAYOUT_SPAN:
+            if predictor is not None:
+                raise ValueError("a layout other than the default takes worst-case room")
+            rc = lib().sd_plan_create_layout(energy.handle, self.count, arr, _ptr(w), shared,
+                                             _ptr(lam), int(layout), ctypes.byref(h),
+                                             _ptr(self.item_status))
+        elif predictor is None:
             rc = lib().sd_plan_create(energy.handle, self.count, arr, _ptr(w), shared, _ptr(lam),
                                       ctypes.byref(h), _ptr(self.item_status))
         else:

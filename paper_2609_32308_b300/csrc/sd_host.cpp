@@ -205,7 +205,31 @@ struct HostLattice {
   std::vector<int64_t> e_cost;
   double qmax_sum = 0.0;  // sum over codon positions of the largest codon cost (FP64)
   std::vector<int32_t> caps;  // room of each candidate list (empty: worst case)
+  int layout = SD_LAYOUT_SPAN;  // layout of the full tables
 };
+
+// Entries of each full table in a layout (see SdDesign::layout).
+int64_t table_cells(const HostLattice &L) {
+  const int64_t n = L.n, N = L.N;
+  if (L.layout == SD_LAYOUT_SQUARE) return N * N;
+  if (L.layout == SD_LAYOUT_PACKED) {
+    int64_t c = 0;
+    for (int v = 0; v < N; v++) c += N - L.lstart[L.layer[v] + 1];
+    return c;
+  }
+  return n * (n + 1) / 2 * SD_SLOTS;
+}
+
+// Row offsets of the forward-packed layout.
+std::vector<int64_t> packed_offsets(const HostLattice &L) {
+  std::vector<int64_t> off(L.N);
+  int64_t c = 0;
+  for (int v = 0; v < L.N; v++) {
+    off[v] = c;
+    c += L.N - L.lstart[L.layer[v] + 1];
+  }
+  return off;
+}
 
 // worst-case room of C_b: every state at least five layers before b
 int32_t worst_room(const HostLattice &L, int v) { return L.lstart[std::max(0, L.layer[v] - 4)]; }
@@ -425,6 +449,8 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.n = (int)n;
   d.N = (int)N;
   d.ncell = ncell;
+  d.layout = L.layout;
+  d.table_cells = table_cells(L);
   d.lstart = c.take<int32_t>(n + 2);
   d.layer = c.take<int32_t>(N);
   d.out = c.take<SdEdge>(N * SD_MAXOUT);
@@ -439,11 +465,13 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.fi = c.take<SdFlatEdge>(std::max(L.E, 1));
   d.fi_off = c.take<int32_t>(N + 1);
   const size_t ring = (size_t)SD_RING * (n + 1) * SD_SLOTS;
-  d.H = c.take<int64_t>(ncell * SD_SLOTS);
-  d.V = c.take<int64_t>(ncell * SD_SLOTS * 6);
-  d.S1 = c.take<int64_t>(ncell * SD_SLOTS);
-  d.S2 = c.take<int64_t>(ncell * SD_SLOTS);
-  d.Bv = c.take<int64_t>(ncell * SD_SLOTS);
+  const int64_t tc = std::max<int64_t>(d.table_cells, 1);
+  d.poff = L.layout == SD_LAYOUT_PACKED ? c.take<int64_t>(N) : nullptr;
+  d.H = c.take<int64_t>(tc);
+  d.V = c.take<int64_t>(tc * 6);
+  d.S1 = c.take<int64_t>(tc);
+  d.S2 = c.take<int64_t>(tc);
+  d.Bv = c.take<int64_t>(tc);
   d.Ihat = c.take<int64_t>(ring);
   d.IL = c.take<int64_t>(ring);
   d.Q = c.take<int64_t>(ring * 6);
@@ -494,6 +522,10 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
             cp(d.fo, fo.data(), (size_t)L.E * sizeof(SdFlatEdge)) &&
             cp(d.fi, fi.data(), (size_t)L.E * sizeof(SdFlatEdge)) &&
             cp(d.fo_off, fo_off.data(), (N + 1) * 4) && cp(d.fi_off, fi_off.data(), (N + 1) * 4);
+  if (ok && d.poff) {
+    const std::vector<int64_t> po = packed_offsets(L);
+    ok = cp(d.poff, po.data(), N * 8);
+  }
   return ok ? SD_OK : SD_ECUDA;
 }
 
@@ -502,7 +534,19 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
 namespace {
 int plan_create(const sd_energy *energy, const sd_predictor *pred, double margin, int count,
                 const char *const *proteins, const double *codon_weights, int weights_shared,
-                const double *lambdas, sd_plan **out, int *item_status);
+                const double *lambdas, sd_plan **out, int *item_status, int layout = SD_LAYOUT_SPAN);
+}
+
+extern "C" int sd_plan_create_layout(const sd_energy *energy, int count,
+                                     const char *const *proteins, const double *codon_weights,
+                                     int weights_shared, const double *lambdas, int layout,
+                                     sd_plan **out, int *item_status) {
+  if (layout != SD_LAYOUT_SPAN && layout != SD_LAYOUT_SQUARE && layout != SD_LAYOUT_PACKED) {
+    if (out) *out = nullptr;
+    return SD_EINVAL;
+  }
+  return plan_create(energy, nullptr, 0.0, count, proteins, codon_weights, weights_shared, lambdas,
+                     out, item_status, layout);
 }
 
 extern "C" int sd_plan_create(const sd_energy *energy, int count, const char *const *proteins,
@@ -577,7 +621,7 @@ int presize(sd_predictor *pred, double margin, std::vector<PlanItem> &items) {
 
 int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margin, int count,
                 const char *const *proteins, const double *codon_weights, int weights_shared,
-                const double *lambdas, sd_plan **out, int *item_status) {
+                const double *lambdas, sd_plan **out, int *item_status, int layout) {
   sd_predictor *pred = const_cast<sd_predictor *>(cpred);
   if (!out) return SD_EINVAL;
   *out = nullptr;
@@ -599,6 +643,7 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
       continue;
     }
     it.protein = proteins[k];
+    it.L.layout = layout;
     it.status = build_lattice(proteins[k], w, it.lambda, it.L);
     if (it.status == SD_OK && it.L.n > SD_MAX_NT) it.status = SD_EINVAL;
     if (it.status == SD_OK) it.status = range_check(energy, it.L);
@@ -1172,8 +1217,10 @@ extern "C" int sd_plan_dump(const sd_plan *p, int item, int32_t *layer, int64_t 
   if (cudaDeviceSynchronize() != cudaSuccess) return SD_ECUDA;
   const HostLattice &L = it.L;
   const SdDesign &d = it.d;
-  const int64_t n = L.n, N = L.N, NN = N * N;
-  const int64_t slots = d.ncell * SD_SLOTS;
+  const int64_t N = L.N, NN = N * N;
+  const int64_t slots = d.table_cells;
+  const std::vector<int64_t> po = L.layout == SD_LAYOUT_PACKED ? packed_offsets(L)
+                                                                : std::vector<int64_t>();
   auto fetch = [](std::vector<int64_t> &v, const int64_t *src, int64_t count) {
     v.resize(count);
     return count == 0 ||
@@ -1200,8 +1247,12 @@ extern "C" int sd_plan_dump(const sd_plan *p, int item, int32_t *layer, int64_t 
     for (int bb = L.lstart[L.layer[a] + 1]; bb < N; bb++) {
       const int la = L.layer[a], lb = L.layer[bb];
       const int64_t g = lb - la;
-      const int64_t s = (((g - 1) * (n + 1) - (g - 1) * g / 2) + la) * SD_SLOTS +
-                        (a - L.lstart[la]) * SD_W + (bb - L.lstart[lb]);
+      const int64_t s =
+          L.layout == SD_LAYOUT_SQUARE ? (int64_t)a * N + bb
+          : L.layout == SD_LAYOUT_PACKED
+              ? po[a] + (bb - L.lstart[la + 1])
+              : (((g - 1) * (L.n + 1) - (g - 1) * g / 2) + la) * SD_SLOTS +
+                    (a - L.lstart[la]) * SD_W + (bb - L.lstart[lb]);
       const int64_t q = (int64_t)a * N + bb;
       if (H) H[q] = cv(h[s]);
       if (B) B[q] = cv(b[s]);

@@ -148,9 +148,24 @@ struct SdDesign {
   int64_t *tb;            // [0] energy, [1] path cost, [2] traceback status, [3] overflow
   int32_t *tb_stack;      // traceback work list, 4 ints per task
   int32_t tb_cap;         // tasks
-  int32_t pad2;
+  // Layout of the full tables H, V, B, S1, S2 (one entry per state pair,
+  // V six entries):
+  //   SD_LAYOUT_SPAN   layer pair (i, i+g) of span g at cell D(g) + i, SD_SLOTS
+  //                    state-pair slots per cell (the default; the cells of one
+  //                    span are contiguous, which suits the span wavefront)
+  //   SD_LAYOUT_SQUARE state pair (a, b) at a*N + b (the paper's square arena)
+  //   SD_LAYOUT_PACKED state pair (a, b), b on a later layer than a, at
+  //                    poff[a] + b - lstart[layer(a)+1] (the paper's forward-
+  //                    packed option: no reverse-layer slots)
+  int32_t layout;
   int64_t ncell;          // n(n+1)/2
+  const int64_t *poff;    // N row offsets (SD_LAYOUT_PACKED only)
+  int64_t table_cells;    // state-pair entries of each full table
 };
+
+#define SD_LAYOUT_SPAN 0
+#define SD_LAYOUT_SQUARE 1
+#define SD_LAYOUT_PACKED 2
 
 // Host entry points implemented in sd_kernels.cu.
 #ifdef __cplusplus

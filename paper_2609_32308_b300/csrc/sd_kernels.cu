@@ -75,7 +75,10 @@ struct Lat {
   __device__ Lat(const SdDesign &d) : D(d) {}
   __device__ __forceinline__ int layer(int v) const { return __ldg(&D.layer[v]); }
   __device__ __forceinline__ int lstart(int l) const { return __ldg(&D.lstart[l]); }
+  // entry of state pair (x, y), x on layer lx, y on a later layer ly
   __device__ __forceinline__ int64_t slot(int x, int y, int lx, int ly) const {
+    if (D.layout == SD_LAYOUT_SQUARE) return (int64_t)x * D.N + y;
+    if (D.layout == SD_LAYOUT_PACKED) return __ldg(&D.poff[x]) + (y - lstart(lx + 1));
     return (diag_off(D.n, ly - lx) + lx) * SD_SLOTS + (x - lstart(lx)) * SD_W + (y - lstart(ly));
   }
   // min path cost x -> y; 0 for x == y; +inf without a path
@@ -162,7 +165,8 @@ __device__ __forceinline__ void seg_min(int64_t &v) {
 // Design view for the fill: hot pointers in registers, 32-bit index math
 // (sizes are limited to n <= 12000 nucleotides on the host).
 struct Fv {
-  int n;
+  int n, N, layout;
+  const int64_t *__restrict__ poff;
   const int32_t *__restrict__ lst;
   const SdEdge *__restrict__ oe;
   const SdEdge *__restrict__ ie;
@@ -179,9 +183,12 @@ struct Fv {
   __device__ __forceinline__ int layer(int v) const { return __ldg(lay + v); }
   __device__ __forceinline__ int w(int l) const { return __ldg(lst + l + 1) - __ldg(lst + l); }
   __device__ __forceinline__ int doff(int s) const { return (s - 1) * (n + 1) - (((s - 1) * s) >> 1); }
-  // packed slot of (layer lx, slot sx) -> (layer ly, slot sy), ly > lx
+  // full-table entry of (layer lx, slot sx) -> (layer ly, slot sy), ly > lx
   __device__ __forceinline__ int cs(int lx, int sx, int ly, int sy) const {
-    return (doff(ly - lx) + lx) * SD_SLOTS + sx * SD_W + sy;
+    if (layout == SD_LAYOUT_SPAN) return (doff(ly - lx) + lx) * SD_SLOTS + sx * SD_W + sy;
+    const int a = ls(lx) + sx;
+    if (layout == SD_LAYOUT_SQUARE) return a * N + ls(ly) + sy;
+    return (int)(__ldg(poff + a) + (ls(ly) + sy - ls(lx + 1)));
   }
   __device__ __forceinline__ int rs(int lx, int sx, int ly, int sy) const {
     return (((ly - lx) & (SD_RING - 1)) * (n + 1) + lx) * SD_SLOTS + sx * SD_W + sy;
@@ -652,6 +659,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   const int j = i + g;
   Fv F;
   F.n = n;
+  F.N = D.N;
+  F.layout = D.layout;
+  F.poff = D.poff;
   F.lst = D.lstart;
   F.oe = D.out;
   F.ie = D.in;
@@ -671,7 +681,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     b0 = F.ls(j);
     wb = F.ls(j + 1) - b0;
   }
-  const int cell = active ? (F.doff(g) + i) * SD_SLOTS : 0;
   const int rcell = ((g & (SD_RING - 1)) * (n + 1) + i) * SD_SLOTS;
   const int64_t mlb = fx(T.mlbase);
   const int js = active ? F.ls(j - 1) : 0;  // first state on layer j-1
@@ -703,6 +712,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const int sa = s / SD_W, sb = s % SD_W;
     const bool ok = active && sa < wa && sb < wb;
     const int a = a0 + sa, b = b0 + sb;
+    const int cell = ok ? F.cs(i, sa, j, sb) : 0;  // this state pair's full-table entry
     // gap cell (every thread of the group; at most a few in-edges)
     if (ok) {
       int64_t hv = SD_INF;
@@ -716,7 +726,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         upd(hv, hp + e.cost);
         TERM(1);
       }
-      if (sub == 0) D.H[cell + s] = settle(hv);
+      if (sub == 0) D.H[cell] = settle(hv);
     }
     // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side mismatch
     {
@@ -763,14 +773,14 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         }
         v = settle(v);
         vv[t] = v;
-        if (ok && sub == t % G) D.V[(int64_t)(cell + s) * 6 + t] = v;
+        if (ok && sub == t % G) D.V[(int64_t)cell * 6 + t] = v;
         if (fin(v)) {
           upd(B, v + fx(T.mlintern + T.au[t]));
           TERM(1);
         }
       }
       B = settle(B);
-      if (ok && sub == 0) D.Bv[cell + s] = B;
+      if (ok && sub == 0) D.Bv[cell] = B;
       Bs[s] = B;
     }
     // inner tables of this cell for the two-loops that will enclose it
@@ -847,6 +857,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const int sa = s / SD_W, sb = s % SD_W;
     const bool ok = active && sa < wa && sb < wb;
     const int a = a0 + sa, b = b0 + sb;
+    const int cell = ok ? F.cs(i, sa, j, sb) : 0;
     int64_t s2 = SD_INF;
     if (ok) {
       if (g >= 2 && sub == 0)
@@ -872,7 +883,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     seg_min<G>(s2);
     s2 = settle(s2);
     if (ok && sub == 0) {
-      D.S2[cell + s] = s2;
+      D.S2[cell] = s2;
       // P_S (Eq. partitionable with S) and S1 = min(B, P_S)
       int64_t ps = s2;
       if (g >= 2) {
@@ -894,7 +905,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       ps = settle(ps);
       int64_t s1 = ps;
       if (fin(Bs[s])) upd(s1, Bs[s]);
-      D.S1[cell + s] = s1;
+      D.S1[cell] = s1;
       PSs[s] = ps;
     }
   }
@@ -1009,6 +1020,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     if (tm_k) {
       Fv Fo;
       Fo.n = Do.n;
+      Fo.N = Do.N;
+      Fo.layout = Do.layout;
+      Fo.poff = Do.poff;
       Fo.lst = Do.lstart;
       Fo.oe = Do.out;
       Fo.ie = Do.in;
@@ -1754,10 +1768,10 @@ __global__ void k_count(const SdDesign *__restrict__ designs, unsigned long long
     for (int i = threadIdx.x; i + g <= n; i += blockDim.x) {
       const int j = i + g;
       const int wa = G.lstart(i + 1) - G.lstart(i), wb = G.lstart(j + 1) - G.lstart(j);
-      const int64_t cell = (diag_off(n, g) + i) * SD_SLOTS;
+      const int a0 = G.lstart(i), b0 = G.lstart(j);
       for (int sa = 0; sa < wa; sa++)
         for (int sb = 0; sb < wb; sb++) {
-          const int64_t s = cell + sa * SD_W + sb;
+          const int64_t s = G.slot(a0 + sa, b0 + sb, i, j);
           fd += fin(D.Bv[s]);
           rc += fin(D.S1[s]) + fin(D.S2[s]);
           for (int t = 0; t < 6; t++) rc += fin(D.V[s * 6 + t]);

@@ -196,6 +196,9 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.n = (int)n;
   d.N = (int)N;
   d.ncell = ncell;
+  d.layout = SD_LAYOUT_SPAN;
+  d.table_cells = ncell * SD_SLOTS;
+  d.poff = nullptr;
   d.status_slot = 0;
   d.lstart = (int32_t *)take((n + 2) * 4);
   d.layer = (int32_t *)take(N * 4);

@@ -425,3 +425,34 @@ def test_stream_schedule_of_a_mixed_batch(sd, E1, par1, k):
     assert [(r["mrna"], r["objective_fx"]) for r in plan.results()] == \
         [(r["mrna"], r["objective_fx"]) for r in res]
     plan.free()
+
+
+@pytest.mark.parametrize("layout", [1, 2])
+def test_square_and_packed_layouts_match_the_oracle(sd, E1, par1, layout):
+    """The paper's square arena and forward-packed layout (Sec. 5) of the full
+    tables give the oracle's tables and designs, also for a mixed batch under
+    graph replay at fill group 8."""
+    for A, seed, lam in [(40, 2, 4.0), (60, 4, 4.0), (25, 3, 1.5)]:
+        prot = inputs.random_protein(A, seed)
+        w = inputs.random_codon_weights(seed)
+        o = oracle.run(par1, prot, w, lam)
+        plan = sd.Plan(E1, [prot], w, [lam], layout=layout)
+        plan.run()
+        compare_tables(plan, 0, o)
+        compare_design(plan.results()[0], o, lam)
+        plan.free()
+    batch = inputs.protein_batch([30, 7, 45, 12, 45, 3], seed=99)
+    plan = sd.Plan(E1, [b[0] for b in batch], np.stack([b[1] for b in batch]),
+                   [b[2] for b in batch], layout=layout)
+    plan.group = 8
+    plan.set_graph(True)
+    for _ in range(2):
+        plan.run()
+        for (p, w, lam), r in zip(batch, plan.results()):
+            compare_design(r, oracle.run(par1, p, w, lam), lam)
+    plan.free()
+
+
+def test_layout_rejects_unknown(sd, E1):
+    with pytest.raises(sd.SdError):
+        sd.Plan(E1, ["MK"], inputs.random_codon_weights(1), [1.0], layout=7)
