@@ -174,14 +174,19 @@ def workload(batch: int, rank: int, length: int = LENGTH, lam: float = LAMBDA):
 
 
 def energy_path():
+    """The benchmark's parameter set as a file for the CPU oracle: written by
+    the test inputs' twin of the library's seeded generator (byte-identical
+    to what sd_load_energy(NULL, ENERGY_SEED) builds inside the library)."""
     from paper_2609_32308_b300 import inputs
     d = os.path.join(tempfile.gettempdir(), "sd_bench_params")
-    return inputs.energy_file_for_seed(ENERGY_SEED, d)
+    return inputs.synthetic_energy_file(ENERGY_SEED, d)
 
 
 def load_energy():
+    """The library's seeded synthetic parameter set (a C caller gets the same
+    set with sd_load_energy(NULL, ENERGY_SEED, &e))."""
     import paper_2609_32308_b300 as sd
-    return sd.sd_load_energy(energy_path())
+    return sd.sd_load_energy(None, ENERGY_SEED)
 
 
 # ---------------------------------------------------------------------------

@@ -67,18 +67,35 @@ typedef struct {
   int32_t reserved;
 } sd_result;
 
-/* Load a parameter file (plain text, "SDENERGY 1" format: named integer tables
- * stack[6][6], mismatch_{hairpin,interior,interior_1n,interior_23}[6][4][4],
- * int11[6][6][4][4], int21[6][6][4][4][4], int22[6][6][4][4][4][4],
- * hairpin/bulge/interior[31], terminal_au[6], ninio, max_ninio, ml_closing,
- * ml_intern, ml_base, then "lxc <float>" and the special triloop / tetraloop /
- * hexaloop lists "<sequence> <total>").  Pair types are AU CG GC UA GU UG;
- * two-loop tables are indexed [outer pair][inner pair read from the loop].
- * The model is the Turner-2004 dangle-0 model of Sec. 3 (special hairpins,
- * lonely pairs, minimum hairpin 3, at most 30 unpaired per two-loop).
- * On success *out owns a host copy and a device copy on the current device.
- * Returns SD_OK, SD_EINVAL (unreadable / malformed file), SD_ENOMEM, SD_ECUDA. */
-int sd_load_energy(const char *path, sd_energy **out);
+/* Load a nearest-neighbour parameter set (Sec. 3: the Turner-2004 dangle-0
+ * model with special hairpins, lonely pairs, minimum hairpin 3 and at most 30
+ * unpaired nucleotides per two-loop).
+ *   path_or_null    a parameter file in the plain-text "SDENERGY 1" format:
+ *                   named integer tables stack[6][6],
+ *                   mismatch_{hairpin,interior,interior_1n,interior_23}[6][4][4],
+ *                   int11[6][6][4][4], int21[6][6][4][4][4],
+ *                   int22[6][6][4][4][4][4], hairpin/bulge/interior[31],
+ *                   terminal_au[6], ninio, max_ninio, ml_closing, ml_intern,
+ *                   ml_base ("<name> <count>" then the integers, row-major),
+ *                   then "lxc <float>" and the special triloop / tetraloop /
+ *                   hexaloop lists ("<name> <count>", then "<sequence> <total>"
+ *                   lines).  Pair types are AU CG GC UA GU UG; two-loop tables
+ *                   are indexed [outer pair][inner pair read from the loop].
+ *                   The paper's tables are not shipped (it pins them by digest).
+ *   synthetic_seed  used only when path_or_null is NULL: the library then
+ *                   generates seeded synthetic integer tables (dcal/mol) with
+ *                   Turner-2004 shapes, signs, magnitudes and two-loop rotation
+ *                   symmetries (SplitMix64 random numbers; the same seed gives
+ *                   the same set on every machine).
+ * On success *out owns a host copy and a device copy on the current device;
+ * every call that uses it must run with that device current (else
+ * SD_EINVAL).  Returns SD_OK, SD_EINVAL (unreadable / malformed file, NULL
+ * out), SD_ENOMEM, SD_ECUDA. */
+int sd_load_energy(const char *path_or_null, uint64_t synthetic_seed, sd_energy **out);
+/* Write the parameter set in the text format above (a set loaded from a seed
+ * becomes a file that any reader of the format, or sd_load_energy, loads
+ * back).  Returns SD_OK or SD_EINVAL (NULL argument, unwritable path). */
+int sd_energy_save(const sd_energy *e, const char *path);
 void sd_energy_free(sd_energy *e);
 
 /* Exact design of one protein (Sec. 3, Eq. 1).

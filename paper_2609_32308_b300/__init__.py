@@ -54,7 +54,9 @@ def lib():
                               "`python -m paper_2609_32308_b300.build`")
         L = ctypes.CDLL(LIB_PATH)
         P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
-        L.sd_load_energy.argtypes = [ctypes.c_char_p, ctypes.POINTER(P)]
+        L.sd_load_energy.argtypes = [ctypes.c_char_p, ctypes.c_uint64, ctypes.POINTER(P)]
+        L.sd_energy_save.argtypes = [P, ctypes.c_char_p]
+        L.sd_energy_save.restype = I
         L.sd_energy_free.argtypes = [P]
         L.sd_energy_free.restype = None
         L.sd_design.argtypes = [P, ctypes.c_char_p, P, D, ctypes.POINTER(sd_result)]
@@ -137,14 +139,22 @@ def _ptr(a):
 
 
 class Energy:
-    """Loaded parameter set (host + device copy); frees itself."""
+    """Loaded parameter set (host + device copy); frees itself.  path: a
+    parameter file, or None for the library's seeded synthetic set `seed`."""
 
-    def __init__(self, path: str):
+    def __init__(self, path: str | None = None, seed: int = 0):
         h = ctypes.c_void_p()
-        rc = lib().sd_load_energy(str(path).encode(), ctypes.byref(h))
+        rc = lib().sd_load_energy(None if path is None else str(path).encode(), int(seed),
+                                  ctypes.byref(h))
         if rc != SD_OK:
-            raise SdError(rc, f"sd_load_energy({path})")
+            raise SdError(rc, f"sd_load_energy({path}, {seed})")
         self.handle = h
+
+    def save(self, path: str) -> None:
+        """Write the parameter set in the text format (sd_energy_save)."""
+        rc = lib().sd_energy_save(self.handle, str(path).encode())
+        if rc != SD_OK:
+            raise SdError(rc, "sd_energy_save")
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -152,8 +162,9 @@ class Energy:
             self.handle = None
 
 
-def sd_load_energy(path: str) -> Energy:
-    return Energy(path)
+def sd_load_energy(path: str | None = None, seed: int = 0) -> Energy:
+    """A parameter file, or (path None) the library's seeded synthetic set."""
+    return Energy(path, seed)
 
 
 def _result_dict(r: sd_result, status: int) -> dict:

@@ -20,7 +20,10 @@
 // ---------------------------------------------------------------------------
 // energy parameters
 // ---------------------------------------------------------------------------
+std::string sd_internal_synthetic_text(uint64_t seed);  // sd_synth.cpp
+
 struct sd_energy {
+  std::string text;        // the parameter set in the "SDENERGY 1" text format
   SdParams h;              // host copy
   int32_t hairpin[31];     // raw hairpin length table (lengths 3..30)
   double lxc;              // long-hairpin extrapolation coefficient
@@ -52,14 +55,24 @@ int nt_code(char c) {
 
 }  // namespace
 
-extern "C" int sd_load_energy(const char *path, sd_energy **out) {
+extern "C" int sd_load_energy(const char *path_or_null, uint64_t synthetic_seed,
+                              sd_energy **out) {
   if (!out) return SD_EINVAL;
   *out = nullptr;
-  if (!path) return SD_EINVAL;
-  std::ifstream in(path);
-  if (!in) return SD_EINVAL;
+  std::string text;
+  if (path_or_null) {
+    std::ifstream f(path_or_null);
+    if (!f) return SD_EINVAL;
+    std::ostringstream ss;
+    ss << f.rdbuf();
+    text = ss.str();
+  } else {
+    text = sd_internal_synthetic_text(synthetic_seed);
+  }
+  std::istringstream in(text);
   sd_energy *E = new (std::nothrow) sd_energy();
   if (!E) return SD_ENOMEM;
+  E->text = text;
   SdParams &P = E->h;
   std::memset(&P, 0, sizeof(P));
   std::string word;
@@ -171,6 +184,14 @@ extern "C" int sd_load_energy(const char *path, sd_energy **out) {
   }
   *out = E;
   return SD_OK;
+}
+
+extern "C" int sd_energy_save(const sd_energy *e, const char *path) {
+  if (!e || !path) return SD_EINVAL;
+  std::ofstream f(path, std::ios::binary);
+  if (!f) return SD_EINVAL;
+  f << e->text;
+  return f.good() ? SD_OK : SD_EINVAL;
 }
 
 extern "C" void sd_energy_free(sd_energy *e) {

@@ -22,6 +22,7 @@ per-amino-acid weights u ~ U(0.05, 1] normalised by their maximum.
 from __future__ import annotations
 
 import io
+import itertools
 import math
 import os
 
@@ -239,6 +240,98 @@ def make_energy_params(seed: int, ml_base: int | None = None) -> dict:
                 seen[seq] = int(rng.integers(150, 501))
         P[name] = sorted(seen.items())
     return P
+
+
+class SplitMix64:
+    """SplitMix64 (Steele, Lea and Flood, OOPSLA 2014): a 64-bit counter
+    advanced by 0x9E3779B97F4A7C15, mixed by two xor-shift-multiply rounds.
+    The library's seeded parameter sets (sd_load_energy with no file) draw
+    from the same generator, so both sides produce identical tables."""
+    MASK = (1 << 64) - 1
+
+    def __init__(self, seed: int):
+        self.x = (int(seed) ^ 0x5D5D5D5D5D5D5D5D) & self.MASK
+
+    def next(self) -> int:
+        self.x = (self.x + 0x9E3779B97F4A7C15) & self.MASK
+        z = self.x
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & self.MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & self.MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: int, hi: int) -> int:
+        """Integer in [lo, hi]."""
+        return lo + self.next() % (hi - lo + 1)
+
+
+def synthetic_energy_params(seed: int) -> dict:
+    """The seeded Turner-shaped tables of the library's sd_load_energy(NULL,
+    seed): the recipe of make_energy_params (same ranges, shapes and
+    rotation symmetries) drawn from SplitMix64 in a fixed order."""
+    R = SplitMix64(seed)
+    P: dict = {}
+    st = np.zeros((6, 6), dtype=np.int64)
+    for t in range(6):
+        for s in range(t, 6):
+            if _strength(t) == 1 and _strength(s) == 1:
+                v = R.uniform(-150, 50)
+            else:
+                v = -(50 * (_strength(t) + _strength(s)) - 50) - R.uniform(0, 100)
+            st[t, s] = st[s, t] = v
+    P["stack"] = st
+    for name in ("mismatch_hairpin", "mismatch_interior", "mismatch_interior_1n",
+                 "mismatch_interior_23"):
+        P[name] = np.array([R.uniform(-150, 0) for _ in range(96)], dtype=np.int64).reshape(6, 4, 4)
+    i11 = np.zeros((6, 6, 4, 4), dtype=np.int64)
+    for t, s_, x, y in itertools.product(range(6), range(6), range(4), range(4)):
+        i11[t, s_, x, y] = (i11[s_, t, y, x] if (s_, t, y, x) < (t, s_, x, y)
+                            else R.uniform(-100, 350))
+    P["int11"] = i11
+    P["int21"] = np.array([R.uniform(-100, 350) for _ in range(2304)],
+                          dtype=np.int64).reshape(6, 6, 4, 4, 4)
+    i22 = np.zeros((6, 6, 4, 4, 4, 4), dtype=np.int64)
+    for t, s_, a, b, c, d in itertools.product(range(6), range(6), range(4), range(4), range(4),
+                                               range(4)):
+        i22[t, s_, a, b, c, d] = (i22[s_, t, c, d, a, b] if (s_, t, c, d, a, b) < (t, s_, a, b, c, d)
+                                  else R.uniform(-100, 350))
+    P["int22"] = i22
+
+    def increasing(lo, hi, first):
+        v = np.full(31, INF_ENTRY, dtype=np.int64)
+        v[first:] = sorted(R.uniform(lo, hi) for _ in range(31 - first))
+        return v
+
+    P["hairpin"] = increasing(350, 650, 3)
+    P["bulge"] = increasing(280, 600, 1)
+    P["interior"] = increasing(100, 500, 2)
+    P["terminal_au"] = np.array([50 if _strength(t) != 3 else 0 for t in range(6)],
+                                dtype=np.int64)
+    P["ninio"] = np.array([60], dtype=np.int64)
+    P["max_ninio"] = np.array([300], dtype=np.int64)
+    P["ml_closing"] = np.array([R.uniform(300, 400)], dtype=np.int64)
+    P["ml_intern"] = np.array([R.uniform(-100, 50)], dtype=np.int64)
+    P["ml_base"] = np.array([0], dtype=np.int64)
+    P["lxc"] = 107.856
+    for (name, L), count in zip(SPECIAL_LISTS, (20, 30, 4)):
+        seen = {}
+        while len(seen) < count:
+            t = R.uniform(0, 5)
+            seq = PAIRS[t][0] + "".join(NUC[R.uniform(0, 3)] for _ in range(L - 2)) + PAIRS[t][1]
+            if seq not in seen:
+                seen[seq] = R.uniform(150, 500)
+        P[name] = sorted(seen.items())
+    return P
+
+
+def synthetic_energy_file(seed: int, directory: str) -> str:
+    """Write (once) the file of synthetic_energy_params(seed) and return its path."""
+    os.makedirs(directory, exist_ok=True)
+    path = os.path.join(directory, f"sd_synth_{seed}.par")
+    if not os.path.exists(path):
+        tmp = path + f".tmp{os.getpid()}"
+        write_energy_file(synthetic_energy_params(seed), tmp)
+        os.replace(tmp, path)
+    return path
 
 
 def energy_text(P: dict) -> str:

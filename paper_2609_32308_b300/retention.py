@@ -34,8 +34,8 @@ DEFAULT_WEIGHTS = os.path.join(HERE, "data", "retention_predictor.npy")
 BANDS = 8
 
 
-def corpus(count: int, seed: int, lo: int = 50, hi: int = 1000, mu: float = math.log(300.0),
-           sigma: float = 0.7):
+def corpus(count: int, seed: int, lo: int = 50, hi: int = 2000, mu: float = math.log(400.0),
+           sigma: float = 0.8):
     """Seeded synthetic proteins: log-normal lengths clipped to [lo, hi],
     amino acids from the Swiss-Prot composition, per-protein codon weights,
     lambda drawn from {0, 4}."""
@@ -131,11 +131,12 @@ def load(path: str = DEFAULT_WEIGHTS) -> Predictor:
 
 
 def evaluate(energy: Energy, pred: Predictor, items, margin: float = 2.0,
-             max_nt_sq: float = 1.5e8):
-    """Run every item with worst-case room (the plain schedule) and with
-    predicted room; return the reserved room, the retained candidates, the
-    regrow count, the device bytes and wall times of both, and whether every
-    design is identical."""
+             max_nt_sq: float = 1.5e8, streams: int = 4):
+    """Run every item with the plain schedule (worst-case room, one launch
+    sequence) and with the predicted one (predicted room, designs over
+    `streams` concurrent streams longest predicted work first); return the
+    reserved room, the retained candidates, the regrow count, the device
+    bytes and wall times of both, and whether every design is identical."""
     room_worst = room_pred = regrows = retained = 0
     bytes_worst = bytes_pred = 0
     t_plain = t_pred = 0.0
@@ -157,6 +158,7 @@ def evaluate(energy: Energy, pred: Predictor, items, margin: float = 2.0,
         t0 = time.perf_counter()
         pres = Plan(energy, *args, predictor=pred, margin=margin)
         try:
+            pres.streams = streams
             pres.run()
             r1 = pres.results()
             t_pred += time.perf_counter() - t0
@@ -181,18 +183,16 @@ def evaluate(energy: Energy, pred: Predictor, items, margin: float = 2.0,
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
-    ap.add_argument("--train", type=int, default=960)
-    ap.add_argument("--held-out", type=int, default=240)
-    ap.add_argument("--hi", type=int, default=1000)
+    ap.add_argument("--train", type=int, default=6000)
+    ap.add_argument("--held-out", type=int, default=1600)
+    ap.add_argument("--hi", type=int, default=2000)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--margin", type=float, default=2.0)
     ap.add_argument("--energy-seed", type=int, default=1)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--report", default=None, help="write a JSON summary here")
     args = ap.parse_args()
-    import tempfile
-    pdir = tempfile.mkdtemp(prefix="sd_energy_")
-    energy = Energy(inputs.energy_file_for_seed(args.energy_seed, pdir))
+    energy = Energy(None, args.energy_seed)  # the library's seeded synthetic set
     items = corpus(args.train + args.held_out, args.seed, hi=args.hi)
     tr, ho = items[:args.train], items[args.train:]
     t0 = time.time()

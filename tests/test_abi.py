@@ -46,8 +46,9 @@ def test_host_only_calls_without_gpu(libsd):
     assert libsd.sd_strerror(0) == b"ok"
     assert b"range" in libsd.sd_strerror(-2)
     h = ctypes.c_void_p()
-    libsd.sd_load_energy.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
-    assert libsd.sd_load_energy(b"/nonexistent/params.par", ctypes.byref(h)) == -1
+    libsd.sd_load_energy.argtypes = [ctypes.c_char_p, ctypes.c_uint64,
+                                     ctypes.POINTER(ctypes.c_void_p)]
+    assert libsd.sd_load_energy(b"/nonexistent/params.par", 0, ctypes.byref(h)) == -1
     assert not h.value
 
 
