@@ -68,6 +68,10 @@ def _load():
         lib.orc_hairpin_energy.restype = ctypes.c_int
         lib.orc_twoloop_energy.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p]
         lib.orc_twoloop_energy.restype = ctypes.c_int
+        lib.orc_run_motifs.argtypes = [ctypes.c_char_p, ctypes.c_char_p,
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                       ctypes.c_char_p, ctypes.POINTER(P)]
+        lib.orc_run_motifs.restype = ctypes.c_int
         lib.orc_set_threads.argtypes = [ctypes.c_int]
         lib.orc_set_threads.restype = ctypes.c_int
         _lib = lib
@@ -139,6 +143,27 @@ def run(param_path: str, protein: str, weights, lam: float) -> OracleDesign:
     h = ctypes.c_void_p()
     st = lib.orc_run(param_path.encode(), protein.encode(),
                      w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(lam), ctypes.byref(h))
+    if not h.value:
+        raise ValueError(f"oracle rejected input (code {st})")
+    try:
+        return OracleDesign(h, st)
+    finally:
+        lib.orc_free(h)
+
+
+def run_motifs(param_path: str, protein: str, weights, lam: float, motifs):
+    """Exact design whose mRNA contains none of the motifs (the codon DFA
+    intersected with the motifs' Aho-Corasick automaton, Sec. 3); None when no
+    motif-free synonymous mRNA exists."""
+    lib = _load()
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    assert w.shape == (64,)
+    h = ctypes.c_void_p()
+    st = lib.orc_run_motifs(param_path.encode(), protein.encode(),
+                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(lam),
+                            ",".join(motifs).encode(), ctypes.byref(h))
+    if st == -3:
+        return None
     if not h.value:
         raise ValueError(f"oracle rejected input (code {st})")
     try:

@@ -40,13 +40,17 @@ def synonymous_space(protein: str) -> int:
     return k
 
 
-def brute_force(P: dict, protein: str, weights, lam: float):
-    """Returns (best objective in fixed point, list of optimal mRNAs)."""
+def brute_force(P: dict, protein: str, weights, lam: float, motifs=()):
+    """Returns (best objective in fixed point, list of optimal mRNAs); with
+    motifs, only the mRNAs containing none of them (None, [] if none is
+    left)."""
     choices = [codons_of(aa) for aa in protein]
     best, arg = None, []
     cache = {}
     for combo in itertools.product(*choices):
         r = "".join(combo)
+        if any(m in r for m in motifs):
+            continue
         if r not in cache:
             cache[r] = mfe(P, r)
         cost = sum(qfx(lam, weights[16 * NUC.index(c[0]) + 4 * NUC.index(c[1]) + NUC.index(c[2])])

@@ -317,6 +317,197 @@ static int build_rna_lattice(const char *rna, OLattice *L) {
 }
 
 /* ------------------------------------------------------------------ */
+/* forbidden motifs (Sec. 3): codon DFA x Aho-Corasick automaton         */
+/* ------------------------------------------------------------------ */
+#define MAXPRE 2048
+typedef struct {
+  int n;                    /* matcher states = distinct motif prefixes  */
+  char pre[MAXPRE][33];     /* ordered by (length, sequence)             */
+  int go[MAXPRE][4];        /* longest suffix of pre+c that is a prefix  */
+  int bad[MAXPRE];          /* pre ends with a motif                     */
+} Matcher;
+
+static int pre_cmp(const void *a, const void *b) {
+  const char *x = (const char *)a, *y = (const char *)b;
+  size_t lx = strlen(x), ly = strlen(y);
+  if (lx != ly) return lx < ly ? -1 : 1;
+  return strcmp(x, y);
+}
+
+static int pre_find(const Matcher *M, const char *s) {
+  for (int k = 0; k < M->n; k++)
+    if (strcmp(M->pre[k], s) == 0) return k;
+  return -1;
+}
+
+/* motifs: comma-separated strings over ACGU; returns 0 or -1 */
+static int matcher_build(const char *motifs, Matcher *M) {
+  char mot[64][33];
+  int nm = 0;
+  const char *p = motifs;
+  while (*p) {
+    int len = 0;
+    while (p[len] && p[len] != ',') len++;
+    if (len == 0 || len > 32 || nm >= 64) return -1;
+    memcpy(mot[nm], p, len);
+    mot[nm][len] = 0;
+    for (int k = 0; k < len; k++)
+      if (!strchr("ACGU", mot[nm][k])) return -1;
+    nm++;
+    p += len;
+    if (*p == ',') p++;
+  }
+  M->n = 0;
+  M->pre[M->n++][0] = 0;
+  for (int k = 0; k < nm; k++)
+    for (int l = 1; l <= (int)strlen(mot[k]); l++) {
+      char buf[33];
+      memcpy(buf, mot[k], l);
+      buf[l] = 0;
+      if (pre_find(M, buf) < 0) {
+        if (M->n >= MAXPRE) return -1;
+        strcpy(M->pre[M->n++], buf);
+      }
+    }
+  qsort(M->pre, M->n, sizeof(M->pre[0]), pre_cmp);
+  for (int k = 0; k < M->n; k++) {
+    M->bad[k] = 0;
+    size_t lk = strlen(M->pre[k]);
+    for (int q = 0; q < nm; q++) {
+      size_t lq = strlen(mot[q]);
+      if (lk >= lq && strcmp(M->pre[k] + lk - lq, mot[q]) == 0) M->bad[k] = 1;
+    }
+    for (int c = 0; c < 4; c++) {
+      char t[40];
+      strcpy(t, M->pre[k]);
+      size_t lt = strlen(t);
+      t[lt] = NT[c];
+      t[lt + 1] = 0;
+      const char *u = t;
+      int id;
+      while ((id = pre_find(M, u)) < 0) u++;
+      M->go[k][c] = id;
+    }
+  }
+  return 0;
+}
+
+typedef struct { int q, m; } PState;
+static int pstate_cmp(const void *a, const void *b) {
+  const PState *x = (const PState *)a, *y = (const PState *)b;
+  if (x->q != y->q) return x->q - y->q;
+  return x->m - y->m;
+}
+
+/* Product of a layered lattice with the matcher: states (q, m) reachable
+ * without entering a bad m, the last layer merged into one sink, trimmed to
+ * states reaching the sink; layer by layer, (q, m) order inside a layer.
+ * Returns 0, -3 for an empty language, -1 on failure. */
+static int motif_product(const OLattice *L0, const Matcher *M, OLattice *L) {
+  int n = L0->n;
+  /* states of the product per layer */
+  PState **lay = calloc(n + 1, sizeof(PState *));
+  int *cnt = calloc(n + 1, sizeof(int)), *cap = calloc(n + 1, sizeof(int));
+  typedef struct { int l, a, b, label; int64_t cost; } PEdge; /* a, b: index in layer */
+  PEdge *pe = NULL;
+  int npe = 0, cpe = 0, rc = 0;
+  lay[0] = malloc(sizeof(PState));
+  lay[0][0].q = L0->s;
+  lay[0][0].m = 0;
+  cnt[0] = cap[0] = 1;
+  for (int l = 0; l < n; l++) {
+    /* targets of layer l + 1, then sort them into (q, m) order */
+    for (int pass = 0; pass < 2; pass++) {
+      for (int a = 0; a < cnt[l]; a++) {
+        int q = lay[l][a].q, m = lay[l][a].m;
+        for (int k = L0->out_off[q]; k < L0->out_off[q + 1]; k++) {
+          const OEdge *e = &L0->edges[L0->out_idx[k]];
+          int m2 = M->go[m][e->label];
+          if (M->bad[m2]) continue;
+          PState t = {e->to, l + 1 == n ? 0 : m2};
+          int b = -1;
+          for (int x = 0; x < cnt[l + 1]; x++)
+            if (lay[l + 1][x].q == t.q && lay[l + 1][x].m == t.m) { b = x; break; }
+          if (pass == 0) {
+            if (b < 0) {
+              if (cnt[l + 1] == cap[l + 1]) {
+                cap[l + 1] = cap[l + 1] ? 2 * cap[l + 1] : 8;
+                lay[l + 1] = realloc(lay[l + 1], sizeof(PState) * cap[l + 1]);
+              }
+              lay[l + 1][cnt[l + 1]++] = t;
+            }
+          } else {
+            if (npe == cpe) {
+              cpe = cpe ? 2 * cpe : 64;
+              pe = realloc(pe, sizeof(PEdge) * cpe);
+            }
+            PEdge x = {l, a, b, e->label, e->cost};
+            pe[npe++] = x;
+          }
+        }
+      }
+      if (pass == 0 && cnt[l + 1] > 1) qsort(lay[l + 1], cnt[l + 1], sizeof(PState), pstate_cmp);
+    }
+  }
+  if (cnt[n] == 0) {
+    rc = -3;
+  } else {
+    /* backward trim */
+    int **live = calloc(n + 1, sizeof(int *));
+    for (int l = 0; l <= n; l++) live[l] = calloc(cnt[l] > 0 ? cnt[l] : 1, sizeof(int));
+    live[n][0] = 1;
+    for (int l = n - 1; l >= 0; l--)
+      for (int k = 0; k < npe; k++)
+        if (pe[k].l == l && live[l + 1][pe[k].b]) live[l][pe[k].a] = 1;
+    if (!live[0][0]) {
+      rc = -3;
+    } else {
+      /* renumber */
+      int **nid = calloc(n + 1, sizeof(int *));
+      int N = 0;
+      memset(L, 0, sizeof(*L));
+      L->n = n;
+      L->lstart = malloc(sizeof(int) * (n + 2));
+      int total = 0;
+      for (int l = 0; l <= n; l++) total += cnt[l];
+      L->layer = malloc(sizeof(int) * (total > 0 ? total : 1));
+      for (int l = 0; l <= n; l++) {
+        nid[l] = malloc(sizeof(int) * (cnt[l] > 0 ? cnt[l] : 1));
+        L->lstart[l] = N;
+        for (int a = 0; a < cnt[l]; a++) {
+          nid[l][a] = live[l][a] ? N : -1;
+          if (live[l][a]) L->layer[N++] = l;
+        }
+      }
+      L->lstart[n + 1] = N;
+      L->N = N;
+      L->edges = malloc(sizeof(OEdge) * (npe > 0 ? npe : 1));
+      int E = 0;
+      for (int k = 0; k < npe; k++) {
+        int a = nid[pe[k].l][pe[k].a], b = nid[pe[k].l + 1][pe[k].b];
+        if (a < 0 || b < 0) continue;
+        OEdge e = {a, b, pe[k].label, pe[k].cost};
+        L->edges[E++] = e;
+      }
+      L->E = E;
+      L->s = 0;
+      L->t = N - 1;
+      lattice_index(L);
+      for (int l = 0; l <= n; l++) free(nid[l]);
+      free(nid);
+    }
+    for (int l = 0; l <= n; l++) free(live[l]);
+    free(live);
+  }
+  for (int l = 0; l <= n; l++) free(lay[l]);
+  free(lay);
+  free(cnt);
+  free(cap);
+  free(pe);
+  return rc;
+}
+
+/* ------------------------------------------------------------------ */
 /* loop energies (integer dcal/mol)                                     */
 /* ------------------------------------------------------------------ */
 static int hairpin_len_energy(const OParams *P, int L) {
@@ -1002,6 +1193,29 @@ int orc_run(const char *param_path, const char *protein, const double *w, double
   if (!(lambda >= 0.0) || !isfinite(lambda)) { free(D); return -1; }
   D->lambda = lambda;
   if (build_codon_lattice(protein, w, lambda, &D->L)) { free(D); return -1; }
+  fill(D);
+  traceback(D, protein, w);
+  *out = D;
+  return D->status;
+}
+
+/* design under forbidden motifs (comma-separated); returns the traceback
+ * status, -1 on invalid input, -3 when no motif-free design exists */
+int orc_run_motifs(const char *param_path, const char *protein, const double *w, double lambda,
+                   const char *motifs, orc_design **out) {
+  *out = NULL;
+  orc_design *D = calloc(1, sizeof(orc_design));
+  if (load_params(param_path, &D->P)) { free(D); return -2; }
+  if (!(lambda >= 0.0) || !isfinite(lambda)) { free(D); return -1; }
+  D->lambda = lambda;
+  OLattice L0;
+  if (build_codon_lattice(protein, w, lambda, &L0)) { free(D); return -1; }
+  Matcher *M = malloc(sizeof(Matcher));
+  int rc = matcher_build(motifs, M);
+  if (rc == 0) rc = motif_product(&L0, M, &D->L);
+  free(M);
+  lattice_free(&L0);
+  if (rc != 0) { free(D); return rc; }
   fill(D);
   traceback(D, protein, w);
   *out = D;

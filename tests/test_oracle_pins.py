@@ -14,6 +14,7 @@ Chain of pins (no value here is produced by the CUDA path):
     value, Z <= B_finite, candidates only among finite direct intervals,
     D1 = min(B, P_D); the 30 / 31 unpaired two-loop boundary; lambda limits.
 """
+import itertools
 import math
 import random
 
@@ -412,3 +413,76 @@ def test_oracle_threads_do_not_change_tables(par1):
     assert (a.mrna, a.structure, a.obj_fx) == (b.mrna, b.structure, b.obj_fx)
     for name in ("H", "V", "B", "D1", "D2", "PD", "Ext", "cand"):
         assert np.array_equal(getattr(a, name), getattr(b, name)), name
+
+
+# ----------------------------------------------------------------------
+# forbidden motifs (Sec. 3: codon DFA x Aho-Corasick automaton)
+# ----------------------------------------------------------------------
+
+MOTIF_CASES = [("MKLFS", ["CUG", "AAA"], 3), ("LSRWM", ["UCG", "CGA", "AGC"], 15),
+               ("GLSRA", ["CUG", "UCU", "GCA"], 22), ("RLS", ["AGA", "CUU", "UUA"], 5),
+               ("MLS*", ["UAA", "UAG"], 9), ("LRSLR", ["CG", "UUA"], 23)]
+
+
+@pytest.mark.parametrize("prot,motifs,wseed", MOTIF_CASES)
+def test_oracle_motifs_equal_brute_force(par1, P1, prot, motifs, wseed):
+    """The motif-constrained optimum is the brute-force minimum over the
+    synonymous mRNAs that contain no motif (Eq. 1 restricted to the motif-free
+    language), at lambda 0 and > 0."""
+    w = inputs.random_codon_weights(wseed)
+    for lam in (0.0, 4.0):
+        o = oracle.run_motifs(par1, prot, w, lam, motifs)
+        best, arg = brute.brute_force(P1, prot, w, lam, motifs)
+        assert best is not None, "every test case has a motif-free design"
+        assert o is not None and o.status == 0
+        assert o.obj_fx == best and o.mrna in arg
+        assert not any(m in o.mrna for m in motifs)
+        assert evaluate.energy(P1, o.mrna, o.structure) == o.energy
+        plain = oracle.run(par1, prot, w, lam)
+        assert o.obj_fx >= plain.obj_fx
+
+
+def _walk_states(prot, motifs):
+    """States (layer, codon-trie state, matcher prefix) visited by every
+    motif-free synonymous mRNA, the last layer merged: the trimmed product."""
+    seen = set()
+    prefixes = {""} | {m[:l] for m in motifs for l in range(1, len(m) + 1)}
+    for combo in itertools.product(*[brute.codons_of(a) for a in prot]):
+        r = "".join(combo)
+        if any(m in r for m in motifs):
+            continue
+        cur = ""
+        for k in range(len(r) + 1):
+            # codon-trie state: the prefix of the current codon
+            q = r[3 * (k // 3):k] if k % 3 else ""
+            seen.add((k, k // 3, q, cur if k < len(r) else ""))
+            if k < len(r):
+                t = cur + r[k]
+                while t not in prefixes:
+                    t = t[1:]
+                cur = t
+    return seen
+
+
+@pytest.mark.parametrize("prot,motifs,wseed", MOTIF_CASES)
+def test_oracle_motif_product_states(par1, prot, motifs, wseed):
+    o = oracle.run_motifs(par1, prot, inputs.random_codon_weights(wseed), 1.0, motifs)
+    counts = np.bincount(o.layer, minlength=o.n + 1)
+    exp = np.zeros(o.n + 1, dtype=int)
+    for (k, _, _, _) in _walk_states(prot, motifs):
+        exp[k] += 1
+    assert counts.tolist() == exp.tolist()
+
+
+def test_oracle_motifs_empty_inventory_and_infeasible(par1):
+    prot = inputs.random_protein(30, 44)
+    w = inputs.random_codon_weights(44)
+    a = oracle.run(par1, prot, w, 4.0)
+    b = oracle.run_motifs(par1, prot, w, 4.0, [])
+    assert (a.mrna, a.obj_fx, a.N) == (b.mrna, b.obj_fx, b.N)
+    assert np.array_equal(a.V, b.V) and np.array_equal(a.D2, b.D2)
+    # unavoidable motifs: the brute force finds no motif-free mRNA either
+    for p, m in (("M", ["AUG"]), ("KK", ["A"]), ("MW", ["GU"]), ("LSRWM", ["UCG", "CGA", "GAU"]),
+                 ("GLSRA", ["GG", "UCU"])):
+        assert oracle.run_motifs(par1, p, w, 1.0, m) is None
+        assert brute.brute_force(read_params(par1), p, w, 1.0, m) == (None, [])
