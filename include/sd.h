@@ -123,6 +123,28 @@ int sd_design_batch(const sd_energy *energy, int count, const char *const *prote
 void sd_result_free(sd_result *r);
 const char *sd_strerror(int code);
 
+/* ---- forbidden motifs (Sec. 3: the codon DFA intersected with a
+ *      deterministic forbidden-motif automaton; Sec. 7.3) ---- */
+
+/* Exact designs whose mRNAs contain none of the given motifs.  The codon DFA
+ * of each protein is intersected with the Aho-Corasick automaton of the motif
+ * set (matcher history crosses codon boundaries; transitions that complete a
+ * motif are removed; states that cannot reach the end are trimmed), which
+ * keeps the layered path model, so the same exact DP runs on the product.
+ *   motifs[nmotifs]  non-empty strings over A C G U of at most 32 nucleotides,
+ *                    at most 64 of them (nmotifs = 0: no constraint).
+ * Products whose layers hold up to 2 states run on the same kernels as plain
+ * designs; wider ones (up to 8 states per layer, at most 32 in-edges per
+ * state) on a wide instance of them with forward-packed full tables; wider
+ * products give the item SD_ESIZE.  An item with no motif-free design gets
+ * SD_EINFEASIBLE.  Otherwise as sd_plan_create / sd_design. */
+int sd_plan_create_motifs(const sd_energy *energy, int count, const char *const *proteins,
+                          const double *codon_weights, int weights_shared, const double *lambdas,
+                          const char *const *motifs, int nmotifs, sd_plan **out,
+                          int *item_status);
+int sd_design_motifs(const sd_energy *energy, const char *protein, const double *codon_weights,
+                     double lambda, const char *const *motifs, int nmotifs, sd_result *out);
+
 /* ---- many values of lambda for one protein (Sec. 10: supported-envelope
  *      and inverse-lambda tools) ---- */
 

@@ -68,6 +68,8 @@ def lib():
         L.sd_strerror.restype = ctypes.c_char_p
         L.sd_plan_create.argtypes = [P, I, P, P, I, P, ctypes.POINTER(P), P]
         L.sd_plan_create_layout.argtypes = [P, I, P, P, I, P, I, ctypes.POINTER(P), P]
+        L.sd_plan_create_motifs.argtypes = [P, I, P, P, I, P, P, I, ctypes.POINTER(P), P]
+        L.sd_design_motifs.argtypes = [P, ctypes.c_char_p, P, D, P, I, ctypes.POINTER(sd_result)]
         L.sd_plan_run.argtypes = [P, P]
         L.sd_plan_launches.argtypes = [P]
         L.sd_plan_launches.restype = ctypes.c_int64
@@ -119,6 +121,7 @@ def lib():
                   "sd_plan_autotune", "sd_plan_set_graph", "sd_plan_retention", "sd_plan_set_dense",
                   "sd_plan_set_streams", "sd_plan_get_streams", "sd_peak_addmin",
                   "sd_design_sweep", "sd_envelope", "sd_inverse_lambda", "sd_plan_create_layout",
+                  "sd_plan_create_motifs", "sd_design_motifs",
                   "sd_plan_create_predicted", "sd_pred_create", "sd_pred_get_params",
                   "sd_pred_set_params", "sd_pred_features", "sd_pred_forward",
                   "sd_pred_gradients", "sd_pred_train_step"):
@@ -239,6 +242,22 @@ def sd_design_batch(energy: Energy, proteins, weights, lambdas) -> list:
             lib().sd_result_free(ctypes.byref(outs[k]))
 
 
+def sd_design_motifs(energy: Energy, protein: str, weights, lam: float, motifs) -> dict:
+    """One exact design whose mRNA contains none of the motifs."""
+    w = np.ascontiguousarray(weights, dtype=np.float64).reshape(64)
+    enc = [m.encode() for m in motifs]
+    marr = (ctypes.c_char_p * max(1, len(enc)))(*enc)
+    r = sd_result()
+    rc = lib().sd_design_motifs(energy.handle, protein.encode(), _ptr(w), float(lam), marr,
+                                len(enc), ctypes.byref(r))
+    try:
+        if rc != SD_OK:
+            raise SdError(rc, "sd_design_motifs")
+        return _result_dict(r, rc)
+    finally:
+        lib().sd_result_free(ctypes.byref(r))
+
+
 def sd_design_sweep(energy: Energy, protein: str, weights, lambdas) -> list:
     """Designs of one protein at several lambdas, one batched launch sequence."""
     k = len(lambdas)
@@ -298,7 +317,7 @@ class Plan:
     """A batch of designs resident on the GPU (sd_plan_* calls)."""
 
     def __init__(self, energy: Energy, proteins, weights, lambdas, predictor=None,
-                 margin: float = 2.0, layout: int = SD_LAYOUT_SPAN):
+                 margin: float = 2.0, layout: int = SD_LAYOUT_SPAN, motifs=None):
         """predictor: a Predictor to presize the candidate lists
         (sd_plan_create_predicted), or None for worst-case room.  layout: the
         layout of the full tables (sd_plan_create_layout; worst-case room)."""
@@ -310,7 +329,15 @@ class Plan:
         arr = (ctypes.c_char_p * self.count)(*self._keep)
         self.item_status = np.zeros(self.count, dtype=np.int32)
         h = ctypes.c_void_p()
-        if layout != SD_LAYOUT_SPAN:
+        if motifs is not None:
+            if predictor is not None or layout != SD_LAYOUT_SPAN:
+                raise ValueError("motif plans take worst-case room and their own layout")
+            self._motifs = [m.encode() for m in motifs]
+            marr = (ctypes.c_char_p * max(1, len(motifs)))(*self._motifs)
+            rc = lib().sd_plan_create_motifs(energy.handle, self.count, arr, _ptr(w), shared,
+                                             _ptr(lam), marr, len(motifs), ctypes.byref(h),
+                                             _ptr(self.item_status))
+        elif layout != SD_LAYOUT_SPAN:
             if predictor is not None:
                 raise ValueError("a layout other than the default takes worst-case room")
             rc = lib().sd_plan_create_layout(energy.handle, self.count, arr, _ptr(w), shared,

@@ -7,7 +7,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", f) for f in ("sd_kernels.cu", "sd_host.cpp", "sd_noalloc.cu", "sd_predictor.cu", "sd_peak.cu", "sd_sweep.cpp", "sd_synth.cpp")]
+SRC = [os.path.join(HERE, "csrc", f) for f in ("sd_kernels.cu", "sd_kernels_wide.cu", "sd_host.cpp", "sd_noalloc.cu", "sd_predictor.cu", "sd_peak.cu", "sd_sweep.cpp", "sd_synth.cpp")]
 DEPS = SRC + [os.path.join(HERE, "csrc", "sd_internal.h"), os.path.join(ROOT, "include", "sd.h")]
 LIB = os.path.join(HERE, "libsd_b300.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -8,7 +8,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <array>
 #include <fstream>
+#include <map>
 #include <new>
 #include <sstream>
 #include <string>
@@ -219,8 +221,10 @@ char translate(int x, int y, int z) {
 
 struct HostLattice {
   int n = 0, N = 0, E = 0;
+  int width = 0;                // most states on one layer
+  int maxin = SD_MAXIN;         // stride of the in-edge lists
   std::vector<int32_t> lstart, layer;
-  std::vector<SdEdge> out, in;  // N*SD_MAXOUT, N*SD_MAXIN
+  std::vector<SdEdge> out, in;  // N*SD_MAXOUT, N*maxin
   std::vector<uint8_t> out_cnt, in_cnt, in_mask, out_mask;
   std::vector<int32_t> e_from, e_to, e_label;  // (from, label) order
   std::vector<int64_t> e_cost;
@@ -229,8 +233,9 @@ struct HostLattice {
   int layout = SD_LAYOUT_SPAN;  // layout of the full tables
 };
 
-// Entries of each full table in a layout (see SdDesign::layout).
-int64_t table_cells(const HostLattice &L) {
+// Entries of each full table in a layout (see SdDesign::layout); wclass is
+// the layer width of the kernel instance the plan runs (slots per cell).
+int64_t table_cells(const HostLattice &L, int wclass) {
   const int64_t n = L.n, N = L.N;
   if (L.layout == SD_LAYOUT_SQUARE) return N * N;
   if (L.layout == SD_LAYOUT_PACKED) {
@@ -238,7 +243,7 @@ int64_t table_cells(const HostLattice &L) {
     for (int v = 0; v < N; v++) c += N - L.lstart[L.layer[v] + 1];
     return c;
   }
-  return n * (n + 1) / 2 * SD_SLOTS;
+  return n * (n + 1) / 2 * wclass * wclass;
 }
 
 // Row offsets of the forward-packed layout.
@@ -265,17 +270,123 @@ int64_t codon_fx(double lambda, double w) {
   return (int64_t)std::llrint(std::ldexp(x, 32));
 }
 
-int build_lattice(const char *protein, const double *w, double lambda, HostLattice &L) {
+struct E3 {
+  int from, to, label;
+  int64_t cost;
+};
+
+// Forbidden-motif automaton (Sec. 3: the Aho-Corasick automaton of the motif
+// set, complete over A C G U): its states are the distinct prefixes of the
+// motifs, numbered by (length, sequence); go[m][c] is the longest suffix of
+// prefix(m) + c that is again a prefix; bad[m] marks the states whose prefix
+// ends with a motif (a transition into one of them completes a motif).
+struct MotifAutomaton {
+  std::vector<std::string> pre;
+  std::vector<std::array<int, 4>> go;
+  std::vector<char> bad;
+  int build(const std::vector<std::string> &motifs) {
+    std::vector<std::string> all{""};
+    for (const auto &m : motifs)
+      for (size_t l = 1; l <= m.size(); l++) all.push_back(m.substr(0, l));
+    std::sort(all.begin(), all.end(), [](const std::string &a, const std::string &b) {
+      return a.size() != b.size() ? a.size() < b.size() : a < b;
+    });
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    pre = all;
+    std::map<std::string, int> id;
+    for (size_t k = 0; k < pre.size(); k++) id[pre[k]] = (int)k;
+    go.assign(pre.size(), {0, 0, 0, 0});
+    bad.assign(pre.size(), 0);
+    for (size_t k = 0; k < pre.size(); k++) {
+      for (const auto &m : motifs)
+        if (pre[k].size() >= m.size() && pre[k].compare(pre[k].size() - m.size(), m.size(), m) == 0)
+          bad[k] = 1;
+      for (int c = 0; c < 4; c++) {
+        std::string t = pre[k] + "ACGU"[c];
+        while (!id.count(t)) t.erase(0, 1);
+        go[k][c] = id[t];
+      }
+    }
+    return (int)pre.size();
+  }
+};
+
+// The product of a layered DFA (states by layer, edges) with the motif
+// automaton: states (q, m) reachable from (source, root) without entering a
+// bad m, the last layer's states merged into one sink, trimmed to the states
+// that reach the sink, numbered layer by layer and by (q, m) inside a layer.
+// Returns SD_OK or SD_EINFEASIBLE (no motif-free design).
+int motif_product(int n, const std::vector<int32_t> &layer_of, const std::vector<E3> &edges,
+                  const MotifAutomaton &M, std::vector<int32_t> &nlayer, std::vector<E3> &nedges) {
+  const int N0 = (int)layer_of.size();
+  std::vector<std::vector<int>> outs(N0);
+  for (size_t e = 0; e < edges.size(); e++) outs[edges[e].from].push_back((int)e);
+  // forward: product states per layer, keyed by (q, m)
+  std::vector<std::map<std::pair<int, int>, int>> at(n + 1);
+  std::vector<std::pair<int, int>> st;  // product state -> (q, m)
+  std::vector<int> st_layer;
+  struct PE {
+    int from, to, label;
+    int64_t cost;
+  };
+  std::vector<PE> pe;
+  auto state = [&](int l, int q, int m) {
+    auto it = at[l].find({q, m});
+    if (it != at[l].end()) return it->second;
+    const int id = (int)st.size();
+    at[l][{q, m}] = id;
+    st.push_back({q, m});
+    st_layer.push_back(l);
+    return id;
+  };
+  state(0, 0, 0);
+  for (int l = 0; l < n; l++) {
+    std::vector<std::pair<std::pair<int, int>, int>> cur(at[l].begin(), at[l].end());
+    for (const auto &kv : cur) {
+      const int q = kv.first.first, m = kv.first.second;
+      for (int e : outs[q]) {
+        const int m2 = M.go[m][edges[e].label];
+        if (M.bad[m2]) continue;
+        const int t = state(l + 1, edges[e].to, l + 1 == n ? 0 : m2);
+        pe.push_back({kv.second, t, edges[e].label, edges[e].cost});
+      }
+    }
+  }
+  if (at[n].empty()) return SD_EINFEASIBLE;
+  // backward: keep states that reach the sink
+  const int P = (int)st.size();
+  std::vector<char> live(P, 0);
+  live[at[n].begin()->second] = 1;
+  std::vector<std::vector<int>> pin(P);
+  for (size_t e = 0; e < pe.size(); e++) pin[pe[e].to].push_back((int)e);
+  for (int l = n; l >= 1; l--)
+    for (const auto &kv : at[l])
+      if (live[kv.second])
+        for (int e : pin[kv.second]) live[pe[e].from] = 1;
+  if (!live[0]) return SD_EINFEASIBLE;
+  // numbering: layer by layer, (q, m) order inside a layer (map order)
+  std::vector<int> nid(P, -1);
+  nlayer.clear();
+  for (int l = 0; l <= n; l++)
+    for (const auto &kv : at[l])
+      if (live[kv.second]) {
+        nid[kv.second] = (int)nlayer.size();
+        nlayer.push_back(l);
+      }
+  nedges.clear();
+  for (const auto &e : pe)
+    if (live[e.from] && live[e.to]) nedges.push_back({nid[e.from], nid[e.to], e.label, e.cost});
+  return SD_OK;
+}
+
+int build_lattice(const char *protein, const double *w, double lambda, HostLattice &L,
+                  const MotifAutomaton *motifs = nullptr) {
   const int A = (int)std::strlen(protein);
   for (int k = 0; k < A; k++)
     if (protein[k] == '*' && k != A - 1) return SD_EINVAL;
   L.n = 3 * A;
   L.lstart.assign(L.n + 2, 0);
   L.layer.clear();
-  struct E3 {
-    int from, to, label;
-    int64_t cost;
-  };
   std::vector<E3> edges;
   L.layer.push_back(0);
   int boundary = 0;
@@ -336,13 +447,31 @@ int build_lattice(const char *protein, const double *w, double lambda, HostLatti
             edges.push_back({pre[x][y], next, z, codon_fx(lambda, w[16 * x + 4 * y + z])});
     boundary = next;
   }
+  if (motifs) {
+    std::vector<int32_t> nlayer;
+    std::vector<E3> nedges;
+    const int rc = motif_product(L.n, L.layer, edges, *motifs, nlayer, nedges);
+    if (rc != SD_OK) return rc;
+    L.layer = nlayer;
+    edges = nedges;
+    for (int l = 0, v = 0; l <= L.n + 1; l++) {
+      while (v < (int)L.layer.size() && L.layer[v] < l) v++;
+      L.lstart[l] = v;
+    }
+  }
   L.N = (int)L.layer.size();
   L.lstart[L.n + 1] = L.N;
   L.E = (int)edges.size();
-  for (int l = 0; l <= L.n; l++)
-    if (L.lstart[l + 1] - L.lstart[l] > SD_W) return SD_EINVAL;
+  L.width = 0;
+  for (int l = 0; l <= L.n; l++) L.width = std::max(L.width, L.lstart[l + 1] - L.lstart[l]);
+  if (L.width > SD_W_WIDE) return SD_ESIZE;
+  std::vector<int> indeg(L.N, 0);
+  int maxdeg = 0;
+  for (const auto &e : edges) maxdeg = std::max(maxdeg, ++indeg[e.to]);
+  if (maxdeg > SD_MAXIN_WIDE) return SD_ESIZE;
+  L.maxin = L.width <= SD_W && maxdeg <= SD_MAXIN ? SD_MAXIN : SD_MAXIN_WIDE;
   L.out.assign((size_t)L.N * SD_MAXOUT, SdEdge{-1, -1, 0});
-  L.in.assign((size_t)L.N * SD_MAXIN, SdEdge{-1, -1, 0});
+  L.in.assign((size_t)L.N * L.maxin, SdEdge{-1, -1, 0});
   L.out_cnt.assign(L.N, 0);
   L.in_cnt.assign(L.N, 0);
   L.in_mask.assign(L.N, 0);
@@ -370,8 +499,8 @@ int build_lattice(const char *protein, const double *w, double lambda, HostLatti
   });
   for (int e : ord) {
     const E3 &x = edges[e];
-    if (L.in_cnt[x.to] >= SD_MAXIN) return SD_EINVAL;
-    L.in[(size_t)x.to * SD_MAXIN + L.in_cnt[x.to]++] = SdEdge{x.from, x.label, x.cost};
+    if (L.in_cnt[x.to] >= L.maxin) return SD_EINVAL;
+    L.in[(size_t)x.to * L.maxin + L.in_cnt[x.to]++] = SdEdge{x.from, x.label, x.cost};
     L.in_mask[x.to] |= 1 << x.label;
   }
   return SD_OK;
@@ -445,7 +574,16 @@ struct sd_plan {
   // multi-stream schedule (sd_plan_set_streams): bins run concurrently
   std::vector<PlanBin> bins;
   cudaEvent_t fork = nullptr;
+  int wclass = SD_W;  // layer width of the kernel instance (SD_W or SD_W_WIDE)
 };
+
+// the kernel instance of a plan's layer width
+static int k_run(const sd_plan *p, const SdDesign *d, int count, const int *ns, const int32_t *cpre,
+                 cudaStream_t st, int64_t *launches, void *const *events) {
+  return p->wclass == SD_W
+             ? sd_k_run(d, count, ns, cpre, p->energy->d, st, launches, events, p->group)
+             : sd_k_run_wide(d, count, ns, cpre, p->energy->d, st, launches, events, 32);
+}
 
 namespace {
 
@@ -460,8 +598,9 @@ struct Carver {
   }
 };
 
-// lay out one design's buffers (base == nullptr: only measure)
-size_t carve(char *base, const HostLattice &L, SdDesign &d) {
+// lay out one design's buffers (base == nullptr: only measure) for the
+// kernel instance of layer width wclass
+size_t carve(char *base, const HostLattice &L, SdDesign &d, int wclass) {
   Carver c{base};
   const int64_t n = L.n, N = L.N;
   const int64_t ncell = n * (n + 1) / 2;
@@ -471,12 +610,13 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.N = (int)N;
   d.ncell = ncell;
   d.layout = L.layout;
-  d.table_cells = table_cells(L);
+  d.table_cells = table_cells(L, wclass);
+  d.maxin = L.maxin;
   d.lstart = c.take<int32_t>(n + 2);
   d.layer = c.take<int32_t>(N);
   d.out = c.take<SdEdge>(N * SD_MAXOUT);
   d.out_cnt = c.take<uint8_t>(N);
-  d.in = c.take<SdEdge>(N * SD_MAXIN);
+  d.in = c.take<SdEdge>(N * L.maxin);
   d.in_cnt = c.take<uint8_t>(N);
   d.in_mask = c.take<uint8_t>(N);
   d.out_mask = c.take<uint8_t>(N);
@@ -485,7 +625,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d) {
   d.fo_off = c.take<int32_t>(N + 1);
   d.fi = c.take<SdFlatEdge>(std::max(L.E, 1));
   d.fi_off = c.take<int32_t>(N + 1);
-  const size_t ring = (size_t)SD_RING * (n + 1) * SD_SLOTS;
+  const size_t ring = (size_t)SD_RING * (n + 1) * wclass * wclass;
   const int64_t tc = std::max<int64_t>(d.table_cells, 1);
   d.poff = L.layout == SD_LAYOUT_PACKED ? c.take<int64_t>(N) : nullptr;
   d.H = c.take<int64_t>(tc);
@@ -527,7 +667,7 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
   for (int v = 0; v < N; v++) rooms[v] = room(L, v);
   std::vector<SdFlatEdge> fo(std::max(L.E, 1)), fi(std::max(L.E, 1));
   std::vector<int32_t> fo_off(N + 1), fi_off(N + 1);
-  sd_internal_flatten((int)N, L.out.data(), L.out_cnt.data(), L.in.data(), L.in_cnt.data(),
+  sd_internal_flatten((int)N, L.out.data(), L.out_cnt.data(), L.in.data(), L.in_cnt.data(), L.maxin,
                       fo.data(), fo_off.data(), fi.data(), fi_off.data());
   auto cp = [](const void *dst, const void *src, size_t bytes) {
     return bytes == 0 || cudaMemcpy(const_cast<void *>(dst), src, bytes, cudaMemcpyHostToDevice) ==
@@ -553,9 +693,63 @@ int upload(const sd_energy *E, const HostLattice &L, const SdDesign &d) {
 }  // namespace
 
 namespace {
+struct MotifAutomaton;
 int plan_create(const sd_energy *energy, const sd_predictor *pred, double margin, int count,
                 const char *const *proteins, const double *codon_weights, int weights_shared,
-                const double *lambdas, sd_plan **out, int *item_status, int layout = SD_LAYOUT_SPAN);
+                const double *lambdas, sd_plan **out, int *item_status, int layout = SD_LAYOUT_SPAN,
+                const MotifAutomaton *motifs = nullptr);
+}
+
+namespace {
+// motif list -> automaton; SD_EINVAL for an empty or non-ACGU motif, more
+// than 64 motifs or a motif longer than 32 nucleotides
+int motif_automaton(const char *const *motifs, int nmotifs, MotifAutomaton &M) {
+  if (nmotifs < 0 || nmotifs > 64 || (nmotifs > 0 && !motifs)) return SD_EINVAL;
+  std::vector<std::string> v;
+  for (int k = 0; k < nmotifs; k++) {
+    if (!motifs[k]) return SD_EINVAL;
+    const std::string m = motifs[k];
+    if (m.empty() || m.size() > 32 || m.find_first_not_of("ACGU") != std::string::npos)
+      return SD_EINVAL;
+    v.push_back(m);
+  }
+  M.build(v);
+  return SD_OK;
+}
+}  // namespace
+
+extern "C" int sd_plan_create_motifs(const sd_energy *energy, int count,
+                                     const char *const *proteins, const double *codon_weights,
+                                     int weights_shared, const double *lambdas,
+                                     const char *const *motifs, int nmotifs, sd_plan **out,
+                                     int *item_status) {
+  MotifAutomaton M;
+  int rc = motif_automaton(motifs, nmotifs, M);
+  if (rc != SD_OK) {
+    if (out) *out = nullptr;
+    return rc;
+  }
+  return plan_create(energy, nullptr, 0.0, count, proteins, codon_weights, weights_shared, lambdas,
+                     out, item_status, SD_LAYOUT_SPAN, &M);
+}
+
+extern "C" int sd_design_motifs(const sd_energy *energy, const char *protein,
+                                const double *codon_weights, double lambda,
+                                const char *const *motifs, int nmotifs, sd_result *out) {
+  if (!energy || !protein || !codon_weights || !out) return SD_EINVAL;
+  sd_plan *p = nullptr;
+  int st = SD_OK;
+  int rc = sd_plan_create_motifs(energy, 1, &protein, codon_weights, 1, &lambda, motifs, nmotifs,
+                                 &p, &st);
+  if (rc != SD_OK) return rc;
+  if (st != SD_OK) {
+    sd_plan_free(p);
+    return st;
+  }
+  rc = sd_plan_run(p, nullptr);
+  if (rc == SD_OK) rc = sd_plan_results(p, out, &st);
+  sd_plan_free(p);
+  return rc != SD_OK ? rc : st;
 }
 
 extern "C" int sd_plan_create_layout(const sd_energy *energy, int count,
@@ -642,7 +836,8 @@ int presize(sd_predictor *pred, double margin, std::vector<PlanItem> &items) {
 
 int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margin, int count,
                 const char *const *proteins, const double *codon_weights, int weights_shared,
-                const double *lambdas, sd_plan **out, int *item_status, int layout) {
+                const double *lambdas, sd_plan **out, int *item_status, int layout,
+                const MotifAutomaton *motifs) {
   sd_predictor *pred = const_cast<sd_predictor *>(cpred);
   if (!out) return SD_EINVAL;
   *out = nullptr;
@@ -665,10 +860,17 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
     }
     it.protein = proteins[k];
     it.L.layout = layout;
-    it.status = build_lattice(proteins[k], w, it.lambda, it.L);
+    it.status = build_lattice(proteins[k], w, it.lambda, it.L, motifs);
     if (it.status == SD_OK && it.L.n > SD_MAX_NT) it.status = SD_EINVAL;
     if (it.status == SD_OK) it.status = range_check(energy, it.L);
   }
+  // the kernel instance: wide when some lattice has layers of more than
+  // SD_W states or states with more than SD_MAXIN in-edges; wide plans keep
+  // the full tables forward-packed
+  for (const auto &it : p->items)
+    if (it.status == SD_OK && (it.L.width > SD_W || it.L.maxin > SD_MAXIN)) p->wclass = SD_W_WIDE;
+  if (p->wclass != SD_W)
+    for (auto &it : p->items) it.L.layout = SD_LAYOUT_PACKED;
   if (pred) {
     int rc = presize(pred, margin, p->items);
     if (rc != SD_OK) {
@@ -679,7 +881,7 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
   for (auto &it : p->items) {
     if (it.status != SD_OK) continue;
     SdDesign d{};
-    total += carve(nullptr, it.L, d);
+    total += carve(nullptr, it.L, d, p->wclass);
     p->max_n = std::max(p->max_n, it.L.n);
   }
   if (item_status)
@@ -703,7 +905,7 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
     p->cpre_host = cpre;
     // default fill group: 8 threads per layer pair when a span holds many
     // layer pairs (a large batch), else 32 (sd_plan_autotune measures)
-    p->group = cpre.back() >= 16384 ? 8 : 32;
+    p->group = p->wclass != SD_W ? 32 : cpre.back() >= 16384 ? 8 : 32;
   }
   if (!p->hdesigns.empty()) {
     if (cudaMalloc(&p->arena, total) != cudaSuccess) {
@@ -716,7 +918,7 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
     for (auto &it : p->items) {
       if (it.dev_index < 0) continue;
       SdDesign &d = p->hdesigns[it.dev_index];
-      off += carve(p->arena + off, it.L, d);
+      off += carve(p->arena + off, it.L, d, p->wclass);
       d.status_slot = it.dev_index;
       it.d = d;
       int rc = upload(energy, it.L, d);
@@ -757,16 +959,15 @@ void record_timing(cudaEvent_t ev, cudaStream_t st) {
 int enqueue(sd_plan *p, cudaStream_t st, int64_t *nl) {
   void *ev[4] = {p->ev[0], p->ev[1], p->ev[2], p->ev[3]};
   if (p->bins.empty())
-    return sd_k_run(p->d_designs, (int)p->hdesigns.size(), p->ns.data(), p->d_cpre,
-                    p->energy->d, st, nl, p->timing ? ev : nullptr, p->group);
+    return k_run(p, p->d_designs, (int)p->hdesigns.size(), p->ns.data(), p->d_cpre, st, nl,
+                 p->timing ? ev : nullptr);
   if (p->timing) record_timing(p->ev[0], st);
   if (cudaEventRecord(p->fork, st) != cudaSuccess) return -1;
   int64_t total = 0;
   for (auto &b : p->bins) {
     int64_t n1 = 0;
     if (cudaStreamWaitEvent(b.st, p->fork, 0) != cudaSuccess) return -1;
-    if (sd_k_run(b.d_designs, (int)b.dev.size(), b.ns.data(), b.d_cpre, p->energy->d, b.st, &n1,
-                 nullptr, p->group))
+    if (k_run(p, b.d_designs, (int)b.dev.size(), b.ns.data(), b.d_cpre, b.st, &n1, nullptr))
       return -1;
     total += n1;
     if (cudaEventRecord(b.done, b.st) != cudaSuccess ||
@@ -936,8 +1137,11 @@ extern "C" int sd_plan_count_ops(sd_plan *p, int64_t *ops) {
   if (nd > 0) {
     unsigned long long *d = nullptr;
     if (cudaMalloc(&d, sizeof(unsigned long long) * nd) != cudaSuccess) return SD_ENOMEM;
-    int rc = sd_k_count_ops(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, d, nullptr,
-                            p->group);
+    int rc = p->wclass == SD_W
+                 ? sd_k_count_ops(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d, d,
+                                  nullptr, p->group)
+                 : sd_k_count_ops_wide(p->d_designs, nd, p->ns.data(), p->d_cpre, p->energy->d,
+                                       d, nullptr, 32);
     bool ok = rc == 0 && cudaMemcpy(h.data(), d, sizeof(unsigned long long) * nd,
                                     cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(d);
@@ -1082,8 +1286,7 @@ int regrow_if_needed(sd_plan *p) {
             cudaMemcpy(d_cpre, cpre.data(), sizeof(int32_t) * cpre.size(),
                        cudaMemcpyHostToDevice) == cudaSuccess;
   int64_t nl = 0;
-  ok = ok && sd_k_run(d_sub, (int)sub.size(), ns.data(), d_cpre, p->energy->d, p->last_stream, &nl,
-                      nullptr, p->group) == 0;
+  ok = ok && k_run(p, d_sub, (int)sub.size(), ns.data(), d_cpre, p->last_stream, &nl, nullptr) == 0;
   ok = ok && cudaStreamSynchronize(p->last_stream) == cudaSuccess;
   cudaFree(d_sub);
   cudaFree(d_cpre);
@@ -1103,7 +1306,8 @@ extern "C" int sd_plan_results(sd_plan *p, sd_result *outs, int *status) {
   if (nd > 0) {
     int64_t *d_counts = nullptr;
     if (cudaMalloc(&d_counts, counts.size() * 8) != cudaSuccess) return SD_ENOMEM;
-    int rc = sd_k_count(p->d_designs, nd, d_counts, nullptr);
+    int rc = p->wclass == SD_W ? sd_k_count(p->d_designs, nd, d_counts, nullptr)
+                               : sd_k_count_wide(p->d_designs, nd, d_counts, nullptr);
     bool ok = rc == 0 && cudaMemcpy(counts.data(), d_counts, counts.size() * 8,
                                     cudaMemcpyDeviceToHost) == cudaSuccess;
     cudaFree(d_counts);
@@ -1171,7 +1375,8 @@ extern "C" int sd_plan_retention(const sd_plan *p, int item, int32_t *counts) {
   if (cudaStreamSynchronize(p->last_stream) != cudaSuccess) return SD_ECUDA;
   int32_t *d = nullptr;
   if (cudaMalloc(&d, sizeof(int32_t) * 8 * A) != cudaSuccess) return SD_ENOMEM;
-  int rc = sd_k_retention(p->d_designs, it.dev_index, d, A, nullptr);
+  int rc = p->wclass == SD_W ? sd_k_retention(p->d_designs, it.dev_index, d, A, nullptr)
+                             : sd_k_retention_wide(p->d_designs, it.dev_index, d, A, nullptr);
   bool ok = rc == 0 && cudaMemcpy(counts, d, sizeof(int32_t) * 8 * A, cudaMemcpyDeviceToHost) ==
                            cudaSuccess;
   cudaFree(d);
@@ -1272,8 +1477,8 @@ extern "C" int sd_plan_dump(const sd_plan *p, int item, int32_t *layer, int64_t 
           L.layout == SD_LAYOUT_SQUARE ? (int64_t)a * N + bb
           : L.layout == SD_LAYOUT_PACKED
               ? po[a] + (bb - L.lstart[la + 1])
-              : (((g - 1) * (L.n + 1) - (g - 1) * g / 2) + la) * SD_SLOTS +
-                    (a - L.lstart[la]) * SD_W + (bb - L.lstart[lb]);
+              : (((g - 1) * (L.n + 1) - (g - 1) * g / 2) + la) * p->wclass * p->wclass +
+                    (a - L.lstart[la]) * p->wclass + (bb - L.lstart[lb]);
       const int64_t q = (int64_t)a * N + bb;
       if (H) H[q] = cv(h[s]);
       if (B) B[q] = cv(b[s]);
@@ -1370,7 +1575,8 @@ extern "C" const char *sd_strerror(int code) {
 // ---------------------------------------------------------------------------
 extern "C" char sd_internal_translate(int x, int y, int z) { return translate(x, y, z); }
 extern "C" void sd_internal_flatten(int N, const SdEdge *out, const uint8_t *out_cnt,
-                                    const SdEdge *in, const uint8_t *in_cnt, SdFlatEdge *fo,
+                                    const SdEdge *in, const uint8_t *in_cnt, int maxin,
+                                    SdFlatEdge *fo,
                                     int32_t *fo_off, SdFlatEdge *fi, int32_t *fi_off) {
   int32_t eo = 0, ei = 0;
   for (int v = 0; v < N; v++) {
@@ -1381,7 +1587,7 @@ extern "C" void sd_internal_flatten(int N, const SdEdge *out, const uint8_t *out
     }
     fi_off[v] = ei;
     for (int k = 0; k < in_cnt[v]; k++) {
-      const SdEdge &e = in[(size_t)v * SD_MAXIN + k];
+      const SdEdge &e = in[(size_t)v * maxin + k];
       fi[ei++] = SdFlatEdge{v, e.other * 4 + e.label, e.cost};
     }
   }

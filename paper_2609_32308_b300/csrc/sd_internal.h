@@ -14,12 +14,24 @@
 #pragma once
 #include <stdint.h>
 
+// Layer width of the kernels' layout: the codon trie has width 2; the
+// library also builds the kernels for width 8 (sd_kernels_wide.cu) for the
+// product of the codon DFA with a forbidden-motif automaton.
+#ifndef SD_W
 #define SD_W 2
+#endif
+#define SD_W_WIDE 8
 #define SD_SLOTS (SD_W * SD_W)
 #define SD_MAXOUT 4      // out-edges per state (one per label in a DFA)
-#define SD_MAXIN 8       // in-edges per state (codon trie: at most 6)
+#define SD_MAXIN 8       // in-edges per state of a codon trie (at most 6)
+#define SD_MAXIN_WIDE 32 // in-edges per state of a product lattice
 #define SD_RING 32       // diagonals kept for the windowed two-loop tables
-#define SD_WN 49         // inner-table entries per cell slot
+// inner-table entries per cell slot: 48 mismatch + 1 bulge, padded to 52 so
+// that every slot and every row of 4 mismatch entries starts on a 32-byte
+// sector (52 * 8 = 13 * 32 bytes)
+#ifndef SD_WN
+#define SD_WN 52
+#endif
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
 #define SD_MAX_NT 12000  // longest mRNA: keeps every table index inside int32
 
@@ -113,7 +125,7 @@ struct SdDesign {
   const int32_t *layer;   // N
   const SdEdge *out;      // N * SD_MAXOUT, by label
   const uint8_t *out_cnt; // N
-  const SdEdge *in;       // N * SD_MAXIN, by (label, source)
+  const SdEdge *in;       // N * maxin, by (label, source)
   const uint8_t *in_cnt;  // N
   const uint8_t *in_mask; // N, bit l set iff some edge with label l enters the state
   const uint8_t *out_mask;// N, bit l set iff the state has an out-edge with label l
@@ -159,6 +171,8 @@ struct SdDesign {
   //                    packed option: no reverse-layer slots)
   int32_t layout;
   int64_t ncell;          // n(n+1)/2
+  int32_t maxin;          // stride of the in-edge lists (SD_MAXIN or SD_MAXIN_WIDE)
+  int32_t pad3;
   const int64_t *poff;    // N row offsets (SD_LAYOUT_PACKED only)
   int64_t table_cells;    // state-pair entries of each full table
 };
@@ -193,11 +207,21 @@ int32_t sd_internal_hairpin_len(const struct sd_energy *E, int L);
 // flat edge lists (fo, fi: E entries each; fo_off, fi_off: N+1) from the
 // per-state lists
 void sd_internal_flatten(int N, const SdEdge *out, const uint8_t *out_cnt, const SdEdge *in,
-                         const uint8_t *in_cnt, SdFlatEdge *fo, int32_t *fo_off, SdFlatEdge *fi,
-                         int32_t *fi_off);
+                         const uint8_t *in_cnt, int maxin, SdFlatEdge *fo, int32_t *fo_off,
+                         SdFlatEdge *fi, int32_t *fi_off);
 int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
 int sd_k_retention(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
                    void *stream);
+// the same entry points of the wide instance (layers of up to SD_W_WIDE states)
+int sd_k_run_wide(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+                  const SdParams *d_params, void *stream, int64_t *launches,
+                  void *const *events, int group);
+int sd_k_count_ops_wide(const SdDesign *d_designs, int count, const int *ns,
+                        const int32_t *d_cpre, const SdParams *d_params,
+                        unsigned long long *d_ops, void *stream, int group);
+int sd_k_count_wide(const SdDesign *d_designs, int count, int64_t *d_out, void *stream);
+int sd_k_retention_wide(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
+                        void *stream);
 #ifdef __cplusplus
 }
 #endif

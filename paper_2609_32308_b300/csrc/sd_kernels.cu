@@ -32,6 +32,14 @@
 
 #include "sd_internal.h"
 
+// The host entry points of this file; the wide instance (SD_W > 2, compiled
+// from sd_kernels_wide.cu) carries the suffix _wide.
+#if SD_W == 2
+#define SD_KFN(name) name
+#else
+#define SD_KFN(name) name##_wide
+#endif
+
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -54,6 +62,19 @@ __device__ __forceinline__ T ro(const T *p) {
   return __ldg(p);
 #else
   return *p;
+#endif
+}
+// The inner-type table W is streamed (each entry read a few times per span,
+// the whole ring per launch): with SD_W_CG its reads are cached in L2 only,
+// leaving L1 to the small, hot edge, layer and gap data.
+#ifndef SD_W_CG
+#define SD_W_CG 1
+#endif
+__device__ __forceinline__ int64_t ro_w(const int64_t *p) {
+#if SD_W_CG
+  return __ldcg(p);
+#else
+  return ro(p);
 #endif
 }
 __device__ __forceinline__ bool fin(int64_t v) { return v < SD_FINLIM; }
@@ -106,7 +127,7 @@ struct Lat {
   __device__ __forceinline__ int nout(int v) const { return D.out_cnt[v]; }
   __device__ __forceinline__ int nin(int v) const { return D.in_cnt[v]; }
   __device__ __forceinline__ SdEdge out(int v, int k) const { return D.out[v * SD_MAXOUT + k]; }
-  __device__ __forceinline__ SdEdge in(int v, int k) const { return D.in[v * SD_MAXIN + k]; }
+  __device__ __forceinline__ SdEdge in(int v, int k) const { return D.in[v * D.maxin + k]; }
   __device__ __forceinline__ int out_with_label(int v, int lab) const {
     for (int k = 0; k < nout(v); k++)
       if (D.out[v * SD_MAXOUT + k].label == lab) return k;
@@ -165,7 +186,7 @@ __device__ __forceinline__ void seg_min(int64_t &v) {
 // Design view for the fill: hot pointers in registers, 32-bit index math
 // (sizes are limited to n <= 12000 nucleotides on the host).
 struct Fv {
-  int n, N, layout;
+  int n, N, layout, maxin;
   const int64_t *__restrict__ poff;
   const int32_t *__restrict__ lst;
   const SdEdge *__restrict__ oe;
@@ -201,7 +222,7 @@ struct Fv {
   __device__ __forceinline__ int nout(int v) const { return on[v]; }
   __device__ __forceinline__ int nin(int v) const { return in_[v]; }
   __device__ __forceinline__ SdEdge out(int v, int k) const { return oe[v * SD_MAXOUT + k]; }
-  __device__ __forceinline__ SdEdge in(int v, int k) const { return ie[v * SD_MAXIN + k]; }
+  __device__ __forceinline__ SdEdge in(int v, int k) const { return ie[v * maxin + k]; }
   // V of a cell of an earlier span (read-only path) ...
   __device__ __forceinline__ void v6(int idx, int64_t (&vv)[6]) const {
     const longlong2 *p = reinterpret_cast<const longlong2 *>(V + (int64_t)idx * 6);
@@ -227,12 +248,12 @@ struct Fv {
 };
 
 // Gap values of the two ends of a layer pair, staged in shared memory per
-// group: hl[l][c*2 + s] = H(slot s of layer i -> slot c of layer i+l),
-// hr[l][c*2 + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW;
+// group: hl[l][c*W + s] = H(slot s of layer i -> slot c of layer i+l),
+// hr[l][c*W + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW;
 // the two-loop options read them many times.
 constexpr int SD_GAPW = SD_MAXTWO + 1;
 struct GapStage {
-  int64_t hl[SD_GAPW][4], hr[SD_GAPW][4];
+  int64_t hl[SD_GAPW][SD_SLOTS], hr[SD_GAPW][SD_SLOTS];
 };
 
 // minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
@@ -361,7 +382,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int l = right ? ly - lv : lv - lx;
       int64_t h = 0;
       if (l > 0) {
-        h = right ? GS.hr[l][sv * 2 + sy] : GS.hl[l][sv * 2 + sx];
+        h = right ? GS.hr[l][sv * SD_W + sy] : GS.hl[l][sv * SD_W + sx];
         if (!fin(h)) continue;
       } else if (sv != sy) {
         continue;
@@ -369,7 +390,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       if (l >= 2) {
         // bulge: bulge[l] + AU(t) + AU(inner); best inner type from the inner table
         const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
-        const int64_t w = ro(D.W + (int64_t)rc * SD_WN + 48);
+        const int64_t w = ro_w(D.W + (int64_t)rc * SD_WN + 48);
         if (!fin(w)) continue;
         upd6<COUNT>(qv, tm, w + h + fx(T.bulge[l]), 2, ops, [&](int t) { return T.au[t]; });
       } else {
@@ -404,7 +425,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int a = 0; a < nox; a++) {
           const SdEdge ec = F.out(x, a);
           const int p = ec.label, cs = ec.other - lx1s;
-          const int64_t w = ro(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR);
+          const int64_t w = ro_w(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR);
           if (!fin(w)) continue;
           const int64_t base = w + ec.cost + r1.cost + e0;
           for (int b2 = 0; b2 < niy; b2++) {
@@ -472,7 +493,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         for (int b = 0; b < niy; b++) {
           const SdEdge er = F.in(y, b);
           const int r = er.label, ds = er.other - ly1s;
-          const int64_t wv = ro(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r);
+          const int64_t wv = ro_w(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r);
           if (!fin(wv)) continue;
           const int64_t base = wv + er.cost + p2.cost + e0;
           for (int a = 0; a < nox; a++) {
@@ -528,7 +549,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
           continue;
       } else {
-        wv = ro(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR);
+        wv = ro_w(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR);
         if (!fin(wv)) continue;
       }
       for (int a = 0; a < nox; a++) {
@@ -589,13 +610,18 @@ constexpr int IL_PAIRS = 375;
 // same position inside the codon at both ends, so the same layer types and
 // mostly the same branches); a block of 3 warps covers 3 * 32/G consecutive
 // layer pairs.
+#ifndef SD_FILL_WARPS
+#define SD_FILL_WARPS 3  // warps per block for groups of 8 or 16 (a multiple of 3)
+#endif
 template <int G>
 struct FillShape {
-  static constexpr int threads = G == 32 ? 128 : 96;
+  // wide layers (SD_W > 2) stage large gap vectors: one group per block
+  static constexpr int threads = G == 32 ? (SD_W > 2 ? 32 : 128) : 32 * SD_FILL_WARPS;
   static constexpr int pairs = threads / G;
   __device__ static int pair_index(int bx) {
     const int warp = (int)threadIdx.x >> 5, grp = ((int)threadIdx.x & 31) / G;
-    return G == 32 ? bx * pairs + warp : bx * pairs + warp + 3 * grp;
+    return G == 32 ? bx * pairs + warp
+                   : bx * pairs + warp % 3 + 3 * (grp + (32 / G) * (warp / 3));
   }
 };
 
@@ -661,6 +687,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   F.n = n;
   F.N = D.N;
   F.layout = D.layout;
+  F.maxin = D.maxin;
   F.poff = D.poff;
   F.lst = D.lstart;
   F.oe = D.out;
@@ -688,15 +715,15 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   GapStage &GS = s_gap[threadIdx.x / G];
   {
     const int lmax = min(SD_GAPW - 1, g - 1);  // spans below g only (this span is not filled yet)
-    for (int q = sub; q < SD_GAPW * 4; q += G) {
-      const int l = q >> 2, c = (q >> 1) & 1, sn = q & 1;
+    for (int q = sub; q < SD_GAPW * SD_SLOTS; q += G) {
+      const int l = q / SD_SLOTS, c = (q / SD_W) % SD_W, sn = q % SD_W;
       int64_t vl = SD_INF, vr = SD_INF;
       if (active && l <= lmax) {
         if (sn < wa && c < F.w(i + l)) vl = l == 0 ? (c == sn ? 0 : SD_INF) : ro(F.H + F.cs(i, sn, i + l, c));
         if (sn < wb && c < F.w(j - l)) vr = l == 0 ? (c == sn ? 0 : SD_INF) : ro(F.H + F.cs(j - l, c, j, sn));
       }
-      GS.hl[l][c * 2 + sn] = vl;
-      GS.hr[l][c * 2 + sn] = vr;
+      GS.hl[l][c * SD_W + sn] = vl;
+      GS.hr[l][c * SD_W + sn] = vr;
     }
     __syncwarp();
   }
@@ -718,7 +745,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       int64_t hv = SD_INF;
       const int nib = F.nin(b);
 #pragma unroll
-      for (int k = 0; k < SD_MAXIN; k++) {
+      for (int k = 0; k < (SD_W == 2 ? SD_MAXIN : SD_MAXIN_WIDE); k++) {
         if (k >= nib) break;
         const SdEdge e = F.in(b, k);
         const int64_t hp = g == 1 ? (e.other == a ? 0 : SD_INF) : ro(F.H + F.cs(i, sa, j - 1, e.other - js));
@@ -738,7 +765,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           const SdEdge e1 = F.out(a, k1), e2 = F.in(b, k2);
           const int cs = e1.other - i1s, ds = e2.other - js;
           const int64_t w =
-              ro(D.W + (int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label);
+              ro_w(D.W + (int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label);
           if (!fin(w)) continue;
           upd(iv, w + e1.cost + e2.cost);
           TERM(3);
@@ -818,19 +845,20 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         const int64_t e = fx(s_ile[q]);
         const int rb = (((ld - lc) & (SD_RING - 1)) * (n + 1) + lc) * SD_SLOTS;
         // slots beyond a layer's width have +inf staged gap values
+#if SD_W == 2
 #pragma unroll
-        for (int cs = 0; cs < SD_W; cs++) {
+        for (int cs = 0; cs < 2; cs++) {
           const int64_t hl0 = GS.hl[l1p][cs * 2], hl1 = GS.hl[l1p][cs * 2 + 1];
           if (!fin(hl0) && !fin(hl1)) continue;
 #pragma unroll
-          for (int ds = 0; ds < SD_W; ds++) {
+          for (int ds = 0; ds < 2; ds++) {
             const int64_t hr0 = GS.hr[l2p][ds * 2], hr1 = GS.hr[l2p][ds * 2 + 1];
             if (!fin(hr0) && !fin(hr1)) continue;
-            const int64_t v = ro(D.Ihat + rb + cs * SD_W + ds);
+            const int64_t v = ro(D.Ihat + rb + cs * 2 + ds);
             if (!fin(v)) continue;
             const int64_t ve = v + e;
 #pragma unroll
-            for (int s = 0; s < SD_SLOTS; s++) {
+            for (int s = 0; s < 4; s++) {
               const int64_t h1 = (s >> 1) ? hl1 : hl0, h2 = (s & 1) ? hr1 : hr0;
               if (fin(h1) && fin(h2)) {
                 upd(lv[s], h1 + ve + h2);
@@ -839,16 +867,44 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
             }
           }
         }
+#else
+#pragma unroll
+        for (int cs = 0; cs < SD_W; cs++) {
+          bool anyl = false;
+#pragma unroll
+          for (int sa = 0; sa < SD_W; sa++) anyl |= fin(GS.hl[l1p][cs * SD_W + sa]);
+          if (!anyl) continue;
+#pragma unroll
+          for (int ds = 0; ds < SD_W; ds++) {
+            bool anyr = false;
+#pragma unroll
+            for (int sb = 0; sb < SD_W; sb++) anyr |= fin(GS.hr[l2p][ds * SD_W + sb]);
+            if (!anyr) continue;
+            const int64_t v = ro(D.Ihat + rb + cs * SD_W + ds);
+            if (!fin(v)) continue;
+            const int64_t ve = v + e;
+#pragma unroll
+            for (int s = 0; s < SD_SLOTS; s++) {
+              const int64_t h1 = GS.hl[l1p][cs * SD_W + s / SD_W];
+              const int64_t h2 = GS.hr[l2p][ds * SD_W + s % SD_W];
+              if (fin(h1) && fin(h2)) {
+                upd(lv[s], h1 + ve + h2);
+                TERM(3);
+              }
+            }
+          }
+        }
+#endif
       }
 #pragma unroll
     for (int s = 0; s < SD_SLOTS; s++) {
       seg_min<G>(lv[s]);
-      if (active && (s >> 1) < wa && (s & 1) < wb && sub == s % G) D.IL[rcell + s] = settle(lv[s]);
+      if (active && s / SD_W < wa && s % SD_W < wb && sub == s % G) D.IL[rcell + s] = settle(lv[s]);
     }
   } else if (active && sub == 0) {
 #pragma unroll
     for (int s = 0; s < SD_SLOTS; s++)
-      if ((s >> 1) < wa && (s & 1) < wb) D.IL[rcell + s] = SD_INF;
+      if (s / SD_W < wa && s % SD_W < wb) D.IL[rcell + s] = SD_INF;
   }
   // Eq. (sparse2) for every slot: edge extensions, then splits at retained
   // candidates (the group splits the candidate list)
@@ -938,7 +994,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   // The (layer pair, slot) cells that some outer type can close are pooled
   // over the groups of the warp and dealt out round-robin, so that a group
   // with one such cell does not idle while another works through four.
-  if constexpr (G == 32) {  // one group per warp: nothing to pool
+  if constexpr (G == 32 || SD_W > 2) {  // one group per warp (or wide slots): no pooling
 #pragma unroll 1
     for (int s = 0; s < SD_SLOTS; s++) {
       const int sa = s / SD_W, sb = s % SD_W;
@@ -1022,6 +1078,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       Fo.n = Do.n;
       Fo.N = Do.N;
       Fo.layout = Do.layout;
+      Fo.maxin = Do.maxin;
       Fo.poff = Do.poff;
       Fo.lst = Do.lstart;
       Fo.oe = Do.out;
@@ -1368,14 +1425,14 @@ constexpr int TL_PAIRS = (SD_MAXTWO + 1) * (SD_MAXTWO + 2) / 2;
 
 // Block-wide search for the first two-loop closing pair type t over the
 // interior a1 -> b1 with value target.  Returns the option's position in
-// the enumeration order, ((u*4 + cs*2 + ds)*6 + ti)*256 + left key*16 + right
+// the enumeration order, (((u*W + cs)*W + ds)*6 + ti)*256 + left key*16 + right
 // key, or NO_OPTION.
 __device__ unsigned long long search_twoloop(const Lat &G, const SdParams &P, int a1, int b1, int t,
                                              int64_t target, unsigned long long *red) {
   unsigned long long best = NO_OPTION;
   const int lx = G.layer(a1), ly = G.layer(b1);
-  for (int u4 = threadIdx.x; u4 < TL_PAIRS * 4; u4 += TB_THREADS) {
-    const int u = u4 >> 2, cs = (u4 >> 1) & 1, ds = u4 & 1;
+  for (int u4 = threadIdx.x; u4 < TL_PAIRS * SD_SLOTS; u4 += TB_THREADS) {
+    const int u = u4 / SD_SLOTS, cs = (u4 / SD_W) % SD_W, ds = u4 % SD_W;
     int l = 0;
     while ((l + 1) * (l + 2) / 2 <= u) l++;
     const int l1 = u - l * (l + 1) / 2, l2 = l - l1;
@@ -1678,8 +1735,8 @@ __global__ void __launch_bounds__(TB_THREADS) k_traceback(const SdDesign *__rest
             if (t0) {
               const int rk = (int)(pos & 15), lk = (int)((pos >> 4) & 15);
               const int ti = (int)((pos >> 8) % 6);
-              const int u4 = (int)((pos >> 8) / 6), u = u4 >> 2;
-              const int cs = (u4 >> 1) & 1, ds = u4 & 1;
+              const int u4 = (int)((pos >> 8) / 6), u = u4 / SD_SLOTS;
+              const int cs = (u4 / SD_W) % SD_W, ds = u4 % SD_W;
               int l = 0;
               while ((l + 1) * (l + 2) / 2 <= u) l++;
               const int l1 = u - l * (l + 1) / 2, l2 = l - l1;
@@ -1810,9 +1867,12 @@ void launch_fill_g(const SdDesign *d_designs, int count, const int *ns, const in
 template <bool COUNT>
 int launch_fill(int G, const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
                 const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
+  if (SD_W > 2) G = 32;  // the wide instance has one group size
   switch (G) {
+#if SD_W == 2
     case 8: launch_fill_g<8, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
     case 16: launch_fill_g<16, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
+#endif
     case 32: launch_fill_g<32, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
     default: return -1;
   }
@@ -1821,7 +1881,7 @@ int launch_fill(int G, const SdDesign *d_designs, int count, const int *ns, cons
 
 }  // namespace
 
-extern "C" int sd_k_retention(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
+extern "C" int SD_KFN(sd_k_retention)(const SdDesign *d_designs, int item, int32_t *d_hist, int ncodons,
                               void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_hist, 0, sizeof(int32_t) * 8 * (ncodons > 0 ? ncodons : 1), st) !=
@@ -1832,7 +1892,7 @@ extern "C" int sd_k_retention(const SdDesign *d_designs, int item, int32_t *d_hi
   return cudaStreamSynchronize(st) == cudaSuccess ? 0 : -1;
 }
 
-extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, void *stream) {
+extern "C" int SD_KFN(sd_k_count)(const SdDesign *d_designs, int count, int64_t *d_out, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
   if (cudaMemsetAsync(d_out, 0, sizeof(int64_t) * 4 * count, st) != cudaSuccess) return -1;
   k_count<<<dim3(64, count), 256, 0, st>>>(d_designs, (unsigned long long *)d_out);
@@ -1842,7 +1902,7 @@ extern "C" int sd_k_count(const SdDesign *d_designs, int count, int64_t *d_out, 
 
 // Counting pass: the same fill with algorithmic-work counters (INT32 slots
 // per design, see TERM); the result tables are identical to sd_k_run's.
-extern "C" int sd_k_count_ops(const SdDesign *d_designs, int count, const int *ns,
+extern "C" int SD_KFN(sd_k_count_ops)(const SdDesign *d_designs, int count, const int *ns,
                               const int32_t *d_cpre, const SdParams *d_params,
                               unsigned long long *d_ops, void *stream, int group) {
   cudaStream_t st = (cudaStream_t)stream;
@@ -1864,7 +1924,7 @@ static void record(void *ev, cudaStream_t st) {
     cudaEventRecord((cudaEvent_t)ev, st);
 }
 
-extern "C" int sd_k_run(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
+extern "C" int SD_KFN(sd_k_run)(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
                         const SdParams *d_params, void *stream, int64_t *launches,
                         void *const *events, int group) {
   cudaStream_t st = (cudaStream_t)stream;

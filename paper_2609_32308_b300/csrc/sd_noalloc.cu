@@ -199,6 +199,7 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.layout = SD_LAYOUT_SPAN;
   d.table_cells = ncell * SD_SLOTS;
   d.poff = nullptr;
+  d.maxin = SD_MAXIN;
   d.status_slot = 0;
   d.lstart = (int32_t *)take((n + 2) * 4);
   d.layer = (int32_t *)take(N * 4);
@@ -257,7 +258,8 @@ extern "C" int sd_design_noalloc(const sd_energy *energy, const char *protein,
   rc = sd_internal_range_check(energy, L.n, L.qmax_sum);
   if (rc != SD_OK) return rc;
   for (int Lh = 0; Lh <= L.n; Lh++) L.hp[Lh] = sd_internal_hairpin_len(energy, Lh);
-  sd_internal_flatten(L.N, L.out, L.out_cnt, L.in, L.in_cnt, L.fo, L.fo_off, L.fi, L.fi_off);
+  sd_internal_flatten(L.N, L.out, L.out_cnt, L.in, L.in_cnt, SD_MAXIN, L.fo, L.fo_off, L.fi,
+                      L.fi_off);
   // set-up, once per device, with that device current
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SD_ECUDA;

@@ -131,7 +131,7 @@ def load(path: str = DEFAULT_WEIGHTS) -> Predictor:
 
 
 def evaluate(energy: Energy, pred: Predictor, items, margin: float = 2.0,
-             max_nt_sq: float = 1.5e8, streams: int = 4):
+             max_nt_sq: float = 1.5e8, streams: int = 1):
     """Run every item with the plain schedule (worst-case room, one launch
     sequence) and with the predicted one (predicted room, designs over
     `streams` concurrent streams longest predicted work first); return the
