@@ -637,6 +637,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d, int wclass) {
   d.IL = c.take<int64_t>(ring);
   d.Q = c.take<int64_t>(ring * 6);
   d.W = c.take<int64_t>(ring * SD_WN);
+  d.Af = c.take<int64_t>(ring * SD_AN);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
   d.cand_cap = L.caps.empty() ? nullptr : c.take<int32_t>(N);

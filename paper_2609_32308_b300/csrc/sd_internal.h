@@ -33,6 +33,7 @@
 #define SD_WN 52
 #endif
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
+#define SD_AN 12         // two-loop factor entries per cell slot (9 used, 96 bytes)
 #define SD_MAX_NT 12000  // longest mRNA: keeps every table index inside int32
 
 // +infinity and the finiteness threshold of the fixed-point arithmetic.
@@ -148,6 +149,12 @@ struct SdDesign {
   // [0,16) 1xn mismatch, [16,32) 2x3 mismatch, [32,48) generic mismatch, each
   // indexed (label into c)*4 + (label out of d); [48] bulge terminal penalty
   int64_t *W;
+  // SD_RING*(n+1)*SLOTS*SD_AN two-loop factors of each cell (a, b) for the
+  // pairs closing one nucleotide outside it (read two spans up): [p] the
+  // 1 x n loops (one unpaired nucleotide p entering a, >= 3 after b's side),
+  // [4 + r] the n x 1 loops (r leaving b), [8] the 2 x 3 and 3 x 2 loops;
+  // each without the outer pair's own mismatch and edge costs
+  int64_t *Af;
   int32_t *cand_cnt;      // N   |C_b|
   const int64_t *cand_off;// N   first entry of C_b
   const int32_t *cand_cap;// N   entries reserved for C_b, or null when each list has its

@@ -408,36 +408,19 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       }
     }
   }
-  // ---- 1 x n: l1 = 1 (nucleotide p after the outer 5' end), l2 >= 1; entries are
-  // the out-edges r1 of the inner pair's 3' end d ----
+  // ---- 1 x 1 and 1 x 2: l1 = 1 (nucleotide p after the outer 5' end), l2 <= 2;
+  // entries are the out-edges r1 of the inner pair's 3' end d (1 x n with
+  // l2 >= 3 comes from the factor table Af below) ----
   {
     const int lc = lx + 1;
-    const int dlo = max(lx + 6, ly - (SD_MAXTWO - 1)), dhi = ly - 1;
+    const int dlo = max(lx + 6, ly - 2), dhi = ly - 1;
     const int k0 = dlo <= dhi ? F.fo_off[F.ls(dlo)] : 0;
     const int k1 = dlo <= dhi ? F.fo_off[F.ls(dhi + 1)] : 0;
     for (int k = k0 + sub; k < k1; k += G) {
       const SdFlatEdge r1 = F.fo[k];
       const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
       const int ld = F.layer(d), ds = d - F.ls(ld), l2 = ly - ld;
-      if (l2 >= 3) {
-        const int lus = F.ls(ld + 1);
-        const int64_t e0 = fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
-        for (int a = 0; a < nox; a++) {
-          const SdEdge ec = F.out(x, a);
-          const int p = ec.label, cs = ec.other - lx1s;
-          const int64_t w = ro_w(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + p * 4 + fR);
-          if (!fin(w)) continue;
-          const int64_t base = w + ec.cost + r1.cost + e0;
-          for (int b2 = 0; b2 < niy; b2++) {
-            const SdEdge r2 = F.in(y, b2);
-            const int64_t h = F.Hh(ld + 1, u - lus, ly - 1, r2.other - ly1s);
-            if (!fin(h)) continue;
-            const int lR = r2.label;
-            upd6<COUNT>(qv, tm, base + h + r2.cost, 5, ops,
-                        [&](int t) { return T.mm1n[t][p * 4 + lR]; });
-          }
-        }
-      } else if (l2 == 1) {
+      if (l2 == 1) {
         if (u != y) continue;
         for (int a = 0; a < nox; a++) {
           const SdEdge ec = F.out(x, a);
@@ -476,64 +459,41 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       }
     }
   }
-  // ---- n x 1: l2 = 1 (nucleotide r before the outer 3' end), l1 >= 2; entries are
-  // the in-edges p2 of the inner pair's 5' end c ----
-  {
-    const int ld = ly - 1;
-    const int clo = lx + 2, chi = min(lx + SD_MAXTWO - 1, ly - 6);
-    const int k0 = clo <= chi ? F.fi_off[F.ls(clo)] : 0;
-    const int k1 = clo <= chi ? F.fi_off[F.ls(chi + 1)] : 0;
+  // ---- 2 x 1: l2 = 1 (nucleotide r before the outer 3' end), l1 = 2; entries
+  // are the in-edges p2 of the inner pair's 5' end c (n x 1 with l1 >= 3 comes
+  // from Af) ----
+  if (g >= 8) {
+    const int ld = ly - 1, lc = lx + 2;
+    const int k0 = F.fi_off[F.ls(lc)], k1 = F.fi_off[F.ls(lc + 1)];
     for (int k = k0 + sub; k < k1; k += G) {
       const SdFlatEdge p2 = F.fi[k];
       const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
-      const int lc = F.layer(c), cs = c - F.ls(lc), l1 = lc - lx;
-      if (l1 >= 3) {
-        const int lws = F.ls(lc - 1);
-        const int64_t e0 = fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
-        for (int b = 0; b < niy; b++) {
-          const SdEdge er = F.in(y, b);
-          const int r = er.label, ds = er.other - ly1s;
-          const int64_t wv = ro_w(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + lL * 4 + r);
-          if (!fin(wv)) continue;
-          const int64_t base = wv + er.cost + p2.cost + e0;
-          for (int a = 0; a < nox; a++) {
-            const SdEdge p1 = F.out(x, a);
-            const int64_t h = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lws);
-            if (!fin(h)) continue;
-            const int fL = p1.label;
-            upd6<COUNT>(qv, tm, base + h + p1.cost, 5, ops,
-                        [&](int t) { return T.mm1n[t][fL * 4 + r]; });
-          }
-        }
-      } else {  // l1 == 2: explicit 2-edge left side
-        for (int b = 0; b < niy; b++) {
-          const SdEdge er = F.in(y, b);
-          const int r = er.label, ds = er.other - ly1s;
-          int64_t vv[6];
-          F.v6(F.cs(lc, cs, ld, ds), vv);
-          for (int a = 0; a < nox; a++) {
-            const SdEdge p1 = F.out(x, a);
-            if (p1.other != w) continue;
-            const int fL = p1.label;
-            const int64_t base = er.cost + p1.cost + p2.cost;
+      const int cs = c - F.ls(lc);
+      for (int b = 0; b < niy; b++) {
+        const SdEdge er = F.in(y, b);
+        const int r = er.label, ds = er.other - ly1s;
+        int64_t vv[6];
+        F.v6(F.cs(lc, cs, ld, ds), vv);
+        for (int a = 0; a < nox; a++) {
+          const SdEdge p1 = F.out(x, a);
+          if (p1.other != w) continue;
+          const int fL = p1.label;
+          const int64_t base = er.cost + p1.cost + p2.cost;
 #pragma unroll
-            for (int ti = 0; ti < 6; ti++) {
-              if (!fin(vv[ti])) continue;
-              const int s = c_rev[ti];
-              upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
-                          [&](int t) { return P.int21[s][t][r * 16 + fL * 4 + lL]; });
-            }
+          for (int ti = 0; ti < 6; ti++) {
+            if (!fin(vv[ti])) continue;
+            const int s = c_rev[ti];
+            upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
+                        [&](int t) { return P.int21[s][t][r * 16 + fL * 4 + lL]; });
           }
         }
       }
     }
   }
-  // ---- 2x2, 2x3, 3x2: entries are (in-edge p2 of c, out-edge r1 of d) ----
-#pragma unroll 1
-  for (int cls = 0; cls < 3; cls++) {
-    const int l1 = cls == 2 ? 3 : 2, l2 = cls == 1 ? 3 : 2;
-    if (g - l1 - l2 < 5) continue;
-    const int lc = lx + l1, ld = ly - l2;
+  // ---- 2x2: entries are (in-edge p2 of c, out-edge r1 of d) (2x3 and 3x2 come
+  // from Af) ----
+  if (g >= 9) {
+    const int lc = lx + 2, ld = ly - 2;
     const int lcs = F.ls(lc), lds = F.ls(ld), lc1s = F.ls(lc - 1), ld1s = F.ls(ld + 1);
     const int pi0 = F.fi_off[lcs], npi = F.fi_off[F.ls(lc + 1)] - pi0;
     const int ro0 = F.fo_off[lds], nro = F.fo_off[F.ls(ld + 1)] - ro0;
@@ -543,15 +503,9 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int cs = p2.v - lcs, ds = r1.v - lds;
       const int w = p2.wl >> 2, lL = p2.wl & 3, u = r1.wl >> 2, fR = r1.wl & 3;
       int64_t vv[6];
-      int64_t wv = SD_INF;
-      if (cls == 0) {
-        F.v6(F.cs(lc, cs, ld, ds), vv);
-        if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
-          continue;
-      } else {
-        wv = ro_w(D.W + (int64_t)F.rs(lc, cs, ld, ds) * SD_WN + 16 + lL * 4 + fR);
-        if (!fin(wv)) continue;
-      }
+      F.v6(F.cs(lc, cs, ld, ds), vv);
+      if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
+        continue;
       for (int a = 0; a < nox; a++) {
         const SdEdge p1 = F.out(x, a);
         const int64_t hl = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lc1s);
@@ -561,34 +515,38 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
           const int64_t hr = F.Hh(ld + 1, u - ld1s, ly - 1, r2.other - ly1s);
           if (!fin(hr)) continue;
           const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
-          const int fL = p1.label, lR = r2.label;
-          if (cls) {
-            upd6<COUNT>(qv, tm, wv + hc + fx(T.interior[5] + T.ninio), 8, ops,
-                        [&](int t) { return T.mm23[t][fL * 4 + lR]; });
-          } else {
-            const int idx = fL * 64 + lL * 16 + fR * 4 + lR;
+          const int idx = p1.label * 64 + lL * 16 + fR * 4 + r2.label;
 #pragma unroll
-            for (int ti = 0; ti < 6; ti++) {
-              if (!fin(vv[ti])) continue;
-              const int s = c_rev[ti];
-              upd6<COUNT>(qv, tm, vv[ti] + hc, 8, ops,
-                          [&](int t) { return P.int22[t][s][idx]; });
-            }
+          for (int ti = 0; ti < 6; ti++) {
+            if (!fin(vv[ti])) continue;
+            const int s = c_rev[ti];
+            upd6<COUNT>(qv, tm, vv[ti] + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
           }
         }
       }
     }
   }
-  // ---- generic internal loops: mismatch edges + the IL table two spans below ----
-  if (g >= 11)
+  // ---- loops reached through the cell one nucleotide inside (c, d): the outer
+  // mismatch edges e1 = x -> c (label p), e2 = d -> y (label r) plus the
+  // cell's tables two spans below: generic internal loops (IL), 1 x n and n x 1
+  // with the long side >= 3 and 2x3 / 3x2 (the factors Af) ----
+  if (g >= 9)
     for (int k = sub; k < nox * niy; k += G) {
       const int a = k / niy, b = k - a * niy;
       const SdEdge e1 = F.out(x, a), e2 = F.in(y, b);
       const int r = F.rs(lx + 1, e1.other - lx1s, ly - 1, e2.other - ly1s);
-      const int64_t il = ro(D.IL + r);
-      if (!fin(il)) continue;
       const int idx = e1.label * 4 + e2.label;
-      upd6<COUNT>(qv, tm, il + e1.cost + e2.cost, 3, ops, [&](int t) { return T.mmI[t][idx]; });
+      const int64_t base = e1.cost + e2.cost;
+      if (g >= 11) {
+        const int64_t il = ro(D.IL + r);
+        if (fin(il)) upd6<COUNT>(qv, tm, il + base, 3, ops, [&](int t) { return T.mmI[t][idx]; });
+      }
+      const int64_t *af = D.Af + (int64_t)r * SD_AN;
+      const int64_t a1 = ro(af + e1.label), a2 = ro(af + 4 + e2.label);
+      const int64_t m1 = a1 < a2 ? a1 : a2;
+      if (fin(m1)) upd6<COUNT>(qv, tm, m1 + base, 3, ops, [&](int t) { return T.mm1n[t][idx]; });
+      const int64_t a23 = ro(af + 8);
+      if (fin(a23)) upd6<COUNT>(qv, tm, a23 + base, 3, ops, [&](int t) { return T.mm23[t][idx]; });
     }
   // ---- multiloop closed by the pair ----
   if (g >= 10 && sub == G - 1) {
@@ -826,6 +784,123 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         }
         Wc[q] = settle(bv);
+      }
+    }
+    // Two-loop factors Af of this cell (a, b) for the pairs closing one
+    // nucleotide outside it (x -> a and b -> y; read by q_slot two spans up).
+    // Everything that does not depend on the outer pair is taken here, once per
+    // cell: the inner pair (c, d), its inner-type table entry, the unpaired
+    // nucleotides beyond a or b and their path costs, read from this layer
+    // pair's staged gap vectors.
+    //   [p]    1 x n: l1 = 1 (nucleotide p enters a), d on layer ld with
+    //          l2 = j + 1 - ld >= 3: W1n(a,d)[p][fR] + r1 + H(u -> b) + size
+    //   [4+r]  n x 1: l2 = 1 (nucleotide r leaves b), c on layer lc with
+    //          l1 = lc - i + 1 >= 3: W1n(c,b)[lL][r] + p2 + H(a -> w) + size
+    //   [8]    2 x 3 and 3 x 2: W23(c,d)[lL][fR] + the unpaired edges + size
+    {
+      int64_t af[9];
+#pragma unroll
+      for (int q = 0; q < 9; q++) af[q] = SD_INF;
+      if (ok && g >= 7) {
+        const int im = D.in_mask[a], om = D.out_mask[b];
+        const int dlo = max(i + 5, j - (SD_MAXTWO - 2)), dhi = j - 2;
+        if (dlo <= dhi) {
+          const int k0 = F.fo_off[F.ls(dlo)], k1 = F.fo_off[F.ls(dhi + 1)];
+          for (int k = k0 + sub; k < k1; k += G) {
+            const SdFlatEdge r1 = F.fo[k];
+            const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
+            const int ld = F.layer(d), l2 = j + 1 - ld;
+            const int64_t h = GS.hr[l2 - 2][(u - F.ls(ld + 1)) * SD_W + sb];
+            if (!fin(h)) continue;
+            const int64_t base =
+                r1.cost + h + fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
+            const int64_t *wrow = D.W + (int64_t)F.rs(i, sa, ld, d - F.ls(ld)) * SD_WN + fR;
+#pragma unroll
+            for (int p = 0; p < 4; p++)
+              if ((im >> p) & 1) {
+                const int64_t w = ro_w(wrow + p * 4);
+                if (fin(w)) {
+                  upd(af[p], w + base);
+                  TERM(5);
+                }
+              }
+          }
+        }
+        const int clo = i + 2, chi = min(i + SD_MAXTWO - 2, j - 5);
+        if (clo <= chi) {
+          const int k0 = F.fi_off[F.ls(clo)], k1 = F.fi_off[F.ls(chi + 1)];
+          for (int k = k0 + sub; k < k1; k += G) {
+            const SdFlatEdge p2 = F.fi[k];
+            const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
+            const int lc = F.layer(c), l1 = lc - i + 1;
+            const int64_t h = GS.hl[l1 - 2][(w - F.ls(lc - 1)) * SD_W + sa];
+            if (!fin(h)) continue;
+            const int64_t base =
+                p2.cost + h + fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
+            const int64_t *wrow = D.W + (int64_t)F.rs(lc, c - F.ls(lc), j, sb) * SD_WN + lL * 4;
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+              if ((om >> r) & 1) {
+                const int64_t wv = ro_w(wrow + r);
+                if (fin(wv)) {
+                  upd(af[4 + r], wv + base);
+                  TERM(5);
+                }
+              }
+          }
+        }
+        if (g >= 8) {
+          const int64_t e23 = fx(T.interior[5] + T.ninio);
+          // 2 x 3: a -> c (p2) on layer i+1; d on layer j-2 -> u (r1) on j-1; H(u -> b)
+          {
+            const int noa = F.nout(a);
+            const int ro0 = F.fo_off[F.ls(j - 2)], nro = F.fo_off[F.ls(j - 1)] - ro0;
+            const int cs0 = F.ls(i + 1), ds0 = F.ls(j - 2), us0 = F.ls(j - 1);
+            for (int k = sub; k < noa * nro; k += G) {
+              const int kp = k / nro, kr = k - kp * nro;
+              const SdEdge p2 = F.out(a, kp);
+              const SdFlatEdge r1 = F.fo[ro0 + kr];
+              const int64_t h = GS.hr[1][((r1.wl >> 2) - us0) * SD_W + sb];
+              if (!fin(h)) continue;
+              const int64_t wv = ro_w(D.W + (int64_t)F.rs(i + 1, p2.other - cs0, j - 2, r1.v - ds0) *
+                                                 SD_WN + 16 + p2.label * 4 + (r1.wl & 3));
+              if (!fin(wv)) continue;
+              upd(af[8], wv + p2.cost + r1.cost + h + e23);
+              TERM(5);
+            }
+          }
+          // 3 x 2: a -> w (H) on layer i+1, w -> c (p2) on i+2; d on j-1 -> b (r1)
+          {
+            const int nib = F.nin(b);
+            const int po0 = F.fo_off[F.ls(i + 1)], npo = F.fo_off[F.ls(i + 2)] - po0;
+            const int ws0 = F.ls(i + 1), cs0 = F.ls(i + 2), ds0 = F.ls(j - 1);
+            for (int k = sub; k < npo * nib; k += G) {
+              const int kp = k / nib, kr = k - kp * nib;
+              const SdFlatEdge p2 = F.fo[po0 + kp];
+              const SdEdge r1 = F.in(b, kr);
+              const int64_t h = GS.hl[1][(p2.v - ws0) * SD_W + sa];
+              if (!fin(h)) continue;
+              const int64_t wv =
+                  ro_w(D.W + (int64_t)F.rs(i + 2, (p2.wl >> 2) - cs0, j - 1, r1.other - ds0) *
+                                 SD_WN + 16 + (p2.wl & 3) * 4 + r1.label);
+              if (!fin(wv)) continue;
+              upd(af[8], wv + p2.cost + r1.cost + h + e23);
+              TERM(5);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 9; q++) seg_min<G>(af[q]);
+      if (ok) {
+        int64_t *Afc = D.Af + (int64_t)(rcell + s) * SD_AN;
+        for (int q = sub; q < 9; q += G) {
+          int64_t v = SD_INF;
+#pragma unroll
+          for (int t = 0; t < 9; t++)
+            if (t == q) v = af[t];
+          Afc[q] = settle(v);
+        }
       }
     }
   }
