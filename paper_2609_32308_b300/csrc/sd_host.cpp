@@ -636,8 +636,10 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d, int wclass) {
   d.Ihat = c.take<int64_t>(ring);
   d.IL = c.take<int64_t>(ring);
   d.Q = c.take<int64_t>(ring * 6);
-  d.W = c.take<int64_t>(ring * SD_WN);
+  d.WB = c.take<int64_t>(ring);
   d.Af = c.take<int64_t>(ring * SD_AN);
+  d.Xc = c.take<int64_t>((size_t)N * 4 * SD_XSPAN * wclass);
+  d.Yr = c.take<int64_t>((size_t)N * 4 * SD_XSPAN * wclass);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
   d.cand_cap = L.caps.empty() ? nullptr : c.take<int32_t>(N);

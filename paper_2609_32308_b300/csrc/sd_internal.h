@@ -26,14 +26,9 @@
 #define SD_MAXIN 8       // in-edges per state of a codon trie (at most 6)
 #define SD_MAXIN_WIDE 32 // in-edges per state of a product lattice
 #define SD_RING 32       // diagonals kept for the windowed two-loop tables
-// inner-table entries per cell slot: 48 mismatch + 1 bulge, padded to 52 so
-// that every slot and every row of 4 mismatch entries starts on a 32-byte
-// sector (52 * 8 = 13 * 32 bytes)
-#ifndef SD_WN
-#define SD_WN 52
-#endif
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
 #define SD_AN 12         // two-loop factor entries per cell slot (9 used, 96 bytes)
+#define SD_XSPAN 32      // spans kept per state in the 1 x n / n x 1 factor tables
 #define SD_MAX_NT 12000  // longest mRNA: keeps every table index inside int32
 
 // +infinity and the finiteness threshold of the fixed-point arithmetic.
@@ -144,11 +139,19 @@ struct SdDesign {
   int64_t *Ihat;          // SD_RING*(n+1)*SLOTS inner pair + its loop-side mismatch
   int64_t *IL;            // SD_RING*(n+1)*SLOTS generic internal loops below a pair
   int64_t *Q;             // SD_RING*(n+1)*SLOTS*6 closed-interior values per outer type
-  // SD_RING*(n+1)*SLOTS*SD_WN inner tables of each cell (c,d): the minimum
-  // over the inner pair types of V plus one loop-side term:
-  // [0,16) 1xn mismatch, [16,32) 2x3 mismatch, [32,48) generic mismatch, each
-  // indexed (label into c)*4 + (label out of d); [48] bulge terminal penalty
-  int64_t *W;
+  // SD_RING*(n+1)*SLOTS bulge inner term of each cell (c,d): the minimum over
+  // the inner pair types of V plus the terminal penalty of the inner pair
+  int64_t *WB;
+  // One-nucleotide-side factors of the 1 x n and n x 1 loops, stored by
+  // state so that a window of 32 consecutive spans is contiguous (ring by span):
+  //   Xc[((a*4 + p)*32 + span)*W + slot of u]: for the cell (a, u), the minimum
+  //     over the in-edges d -> u (label fR) of the edge cost plus the minimum
+  //     over inner types of V(a,d) + mismatch1n(label fR after d, p before a)
+  //   Yr[((b*4 + r)*32 + span)*W + slot of w]: for the cell (w, b), the minimum
+  //     over the out-edges w -> c (label lL) of the edge cost plus the minimum
+  //     over inner types of V(c,b) + mismatch1n(r after b, lL before c)
+  // (N*4*32*W each, W the layer width of the kernel instance)
+  int64_t *Xc, *Yr;
   // SD_RING*(n+1)*SLOTS*SD_AN two-loop factors of each cell (a, b) for the
   // pairs closing one nucleotide outside it (read two spans up): [p] the
   // 1 x n loops (one unpaired nucleotide p entering a, >= 3 after b's side),

@@ -64,19 +64,6 @@ __device__ __forceinline__ T ro(const T *p) {
   return *p;
 #endif
 }
-// The inner-type table W is streamed (each entry read a few times per span,
-// the whole ring per launch): with SD_W_CG its reads are cached in L2 only,
-// leaving L1 to the small, hot edge, layer and gap data.
-#ifndef SD_W_CG
-#define SD_W_CG 1
-#endif
-__device__ __forceinline__ int64_t ro_w(const int64_t *p) {
-#if SD_W_CG
-  return __ldcg(p);
-#else
-  return ro(p);
-#endif
-}
 __device__ __forceinline__ bool fin(int64_t v) { return v < SD_FINLIM; }
 
 __device__ __forceinline__ int64_t diag_off(int64_t n, int64_t g) {
@@ -388,9 +375,9 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         continue;
       }
       if (l >= 2) {
-        // bulge: bulge[l] + AU(t) + AU(inner); best inner type from the inner table
+        // bulge: bulge[l] + AU(t) + AU(inner); best inner type from WB
         const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
-        const int64_t w = ro_w(D.W + (int64_t)rc * SD_WN + 48);
+        const int64_t w = ro(D.WB + rc);
         if (!fin(w)) continue;
         upd6<COUNT>(qv, tm, w + h + fx(T.bulge[l]), 2, ops, [&](int t) { return T.au[t]; });
       } else {
@@ -721,9 +708,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         for (int q = sub; q < no * ni; q += G) {
           const int k2 = q % ni, k1 = q / ni;
           const SdEdge e1 = F.out(a, k1), e2 = F.in(b, k2);
-          const int cs = e1.other - i1s, ds = e2.other - js;
-          const int64_t w =
-              ro_w(D.W + (int64_t)F.rs(i + 1, cs, j - 1, ds) * SD_WN + 32 + e1.label * 4 + e2.label);
+          int64_t vi[6];
+          F.v6(F.cs(i + 1, e1.other - i1s, j - 1, e2.other - js), vi);
+          const int64_t w = best_inner(vi, T.mmI, e2.label * 4 + e1.label);
           if (!fin(w)) continue;
           upd(iv, w + e1.cost + e2.cost);
           TERM(3);
@@ -768,87 +755,110 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       if (ok && sub == 0) D.Bv[cell] = B;
       Bs[s] = B;
     }
-    // inner tables of this cell for the two-loops that will enclose it
+    // inner terms of this cell for the loops that will enclose it: the bulge
+    // term WB (inner pair (a, b)) and the one-nucleotide-side factors X(a, b)
+    // (inner pair (a, d), d -> b) and Y(a, b) (inner pair (c, b), a -> c) of
+    // the 1 x n and n x 1 loops
     if (ok) {
+      if (sub == 0) D.WB[rcell + s] = settle(g >= 5 ? best_au(vv, T.au) : SD_INF);
       const int im = D.in_mask[a], om = D.out_mask[b];
-      int64_t *Wc = D.W + (int64_t)(rcell + s) * SD_WN;
-      for (int q = sub; q < SD_WN; q += G) {
-        int64_t bv = SD_INF;
-        if (g >= 5) {
-          if (q < 48) {
-            const int tab = q >> 4, li = (q >> 2) & 3, lo = q & 3;
-            if (((im >> li) & 1) && ((om >> lo) & 1))
-              bv = best_inner(vv, tab == 0 ? T.mm1n : tab == 1 ? T.mm23 : T.mmI, lo * 4 + li);
-          } else {
-            bv = best_au(vv, T.au);
-          }
+      const int nib = F.nin(b), noa = F.nout(a);
+      const int sp = g & (SD_XSPAN - 1);
+      for (int q = sub; q < 8; q += G) {
+        const int lab = q & 3;
+        int64_t x = SD_INF;
+        if (q < 4) {  // X(a, b)[p = lab]: inner pair (a, d) of span g-1
+          if (!((im >> lab) & 1)) continue;
+          if (g >= 6)
+            for (int k = 0; k < nib; k++) {
+              const SdEdge e = F.in(b, k);
+              int64_t vi[6];
+              F.v6(F.cs(i, sa, j - 1, e.other - js), vi);
+              const int64_t t = best_inner(vi, T.mm1n, e.label * 4 + lab);
+              if (fin(t)) {
+                upd(x, t + e.cost);
+                TERM(2);
+              }
+            }
+          D.Xc[((int64_t)(a * 4 + lab) * SD_XSPAN + sp) * SD_W + sb] = settle(x);
+        } else {  // Y(a, b)[r = lab]: inner pair (c, b) of span g-1
+          if (!((om >> lab) & 1)) continue;
+          if (g >= 6)
+            for (int k = 0; k < noa; k++) {
+              const SdEdge e = F.out(a, k);
+              int64_t vi[6];
+              F.v6(F.cs(i + 1, e.other - i1s, j, sb), vi);
+              const int64_t t = best_inner(vi, T.mm1n, lab * 4 + e.label);
+              if (fin(t)) {
+                upd(x, t + e.cost);
+                TERM(2);
+              }
+            }
+          D.Yr[((int64_t)(b * 4 + lab) * SD_XSPAN + sp) * SD_W + sa] = settle(x);
         }
-        Wc[q] = settle(bv);
       }
     }
     // Two-loop factors Af of this cell (a, b) for the pairs closing one
     // nucleotide outside it (x -> a and b -> y; read by q_slot two spans up).
     // Everything that does not depend on the outer pair is taken here, once per
-    // cell: the inner pair (c, d), its inner-type table entry, the unpaired
-    // nucleotides beyond a or b and their path costs, read from this layer
-    // pair's staged gap vectors.
-    //   [p]    1 x n: l1 = 1 (nucleotide p enters a), d on layer ld with
-    //          l2 = j + 1 - ld >= 3: W1n(a,d)[p][fR] + r1 + H(u -> b) + size
-    //   [4+r]  n x 1: l2 = 1 (nucleotide r leaves b), c on layer lc with
-    //          l1 = lc - i + 1 >= 3: W1n(c,b)[lL][r] + p2 + H(a -> w) + size
-    //   [8]    2 x 3 and 3 x 2: W23(c,d)[lL][fR] + the unpaired edges + size
+    // cell: the inner pair, the unpaired nucleotides beyond a or b and their
+    // path costs (from this layer pair's staged gap vectors):
+    //   [p]    1 x n: l1 = 1 (nucleotide p enters a), the inner pair (a, d) with
+    //          d -> u, u on layer lu, l2 = j + 2 - lu >= 3: X(a,u)[p] + H(u -> b)
+    //          + size / asymmetry
+    //   [4+r]  n x 1: l2 = 1 (nucleotide r leaves b), the inner pair (c, b) with
+    //          w -> c, w on layer lw, l1 = lw - i + 2 >= 3: Y(w,b)[r] + H(a -> w)
+    //          + size / asymmetry
+    //   [8]    2 x 3 and 3 x 2: the inner pair's V with its 2x3 mismatch, the
+    //          unpaired edges, size
     {
       int64_t af[9];
 #pragma unroll
       for (int q = 0; q < 9; q++) af[q] = SD_INF;
       if (ok && g >= 7) {
         const int im = D.in_mask[a], om = D.out_mask[b];
-        const int dlo = max(i + 5, j - (SD_MAXTWO - 2)), dhi = j - 2;
-        if (dlo <= dhi) {
-          const int k0 = F.fo_off[F.ls(dlo)], k1 = F.fo_off[F.ls(dhi + 1)];
-          for (int k = k0 + sub; k < k1; k += G) {
-            const SdFlatEdge r1 = F.fo[k];
-            const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
-            const int ld = F.layer(d), l2 = j + 1 - ld;
-            const int64_t h = GS.hr[l2 - 2][(u - F.ls(ld + 1)) * SD_W + sb];
+        // 1 x n: u on layer lu, l2 = j + 2 - lu in [3, 29], inner span lu - 1 - i >= 5
+        const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
+        if (ulo <= uhi)
+          for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
+            const int lu = F.layer(u), us = u - F.ls(lu), l2 = j + 2 - lu;
+            const int64_t h = GS.hr[j - lu][us * SD_W + sb];
             if (!fin(h)) continue;
             const int64_t base =
-                r1.cost + h + fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
-            const int64_t *wrow = D.W + (int64_t)F.rs(i, sa, ld, d - F.ls(ld)) * SD_WN + fR;
+                h + fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
+            const int64_t *xc =
+                D.Xc + ((int64_t)a * 4 * SD_XSPAN + ((lu - i) & (SD_XSPAN - 1))) * SD_W + us;
 #pragma unroll
             for (int p = 0; p < 4; p++)
               if ((im >> p) & 1) {
-                const int64_t w = ro_w(wrow + p * 4);
-                if (fin(w)) {
-                  upd(af[p], w + base);
-                  TERM(5);
+                const int64_t x = ro(xc + p * SD_XSPAN * SD_W);
+                if (fin(x)) {
+                  upd(af[p], x + base);
+                  TERM(2);
                 }
               }
           }
-        }
-        const int clo = i + 2, chi = min(i + SD_MAXTWO - 2, j - 5);
-        if (clo <= chi) {
-          const int k0 = F.fi_off[F.ls(clo)], k1 = F.fi_off[F.ls(chi + 1)];
-          for (int k = k0 + sub; k < k1; k += G) {
-            const SdFlatEdge p2 = F.fi[k];
-            const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
-            const int lc = F.layer(c), l1 = lc - i + 1;
-            const int64_t h = GS.hl[l1 - 2][(w - F.ls(lc - 1)) * SD_W + sa];
+        // n x 1: w on layer lw, l1 = lw - i + 2 in [3, 29], inner span j - lw - 1 >= 5
+        const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
+        if (wlo <= whi)
+          for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
+            const int lw = F.layer(w), ws = w - F.ls(lw), l1 = lw - i + 2;
+            const int64_t h = GS.hl[lw - i][ws * SD_W + sa];
             if (!fin(h)) continue;
             const int64_t base =
-                p2.cost + h + fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
-            const int64_t *wrow = D.W + (int64_t)F.rs(lc, c - F.ls(lc), j, sb) * SD_WN + lL * 4;
+                h + fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
+            const int64_t *yr =
+                D.Yr + ((int64_t)b * 4 * SD_XSPAN + ((j - lw) & (SD_XSPAN - 1))) * SD_W + ws;
 #pragma unroll
             for (int r = 0; r < 4; r++)
               if ((om >> r) & 1) {
-                const int64_t wv = ro_w(wrow + r);
-                if (fin(wv)) {
-                  upd(af[4 + r], wv + base);
-                  TERM(5);
+                const int64_t y = ro(yr + r * SD_XSPAN * SD_W);
+                if (fin(y)) {
+                  upd(af[4 + r], y + base);
+                  TERM(2);
                 }
               }
           }
-        }
         if (g >= 8) {
           const int64_t e23 = fx(T.interior[5] + T.ninio);
           // 2 x 3: a -> c (p2) on layer i+1; d on layer j-2 -> u (r1) on j-1; H(u -> b)
@@ -862,8 +872,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
               const SdFlatEdge r1 = F.fo[ro0 + kr];
               const int64_t h = GS.hr[1][((r1.wl >> 2) - us0) * SD_W + sb];
               if (!fin(h)) continue;
-              const int64_t wv = ro_w(D.W + (int64_t)F.rs(i + 1, p2.other - cs0, j - 2, r1.v - ds0) *
-                                                 SD_WN + 16 + p2.label * 4 + (r1.wl & 3));
+              int64_t vi[6];
+              F.v6(F.cs(i + 1, p2.other - cs0, j - 2, r1.v - ds0), vi);
+              const int64_t wv = best_inner(vi, T.mm23, (r1.wl & 3) * 4 + p2.label);
               if (!fin(wv)) continue;
               upd(af[8], wv + p2.cost + r1.cost + h + e23);
               TERM(5);
@@ -880,9 +891,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
               const SdEdge r1 = F.in(b, kr);
               const int64_t h = GS.hl[1][(p2.v - ws0) * SD_W + sa];
               if (!fin(h)) continue;
-              const int64_t wv =
-                  ro_w(D.W + (int64_t)F.rs(i + 2, (p2.wl >> 2) - cs0, j - 1, r1.other - ds0) *
-                                 SD_WN + 16 + (p2.wl & 3) * 4 + r1.label);
+              int64_t vi[6];
+              F.v6(F.cs(i + 2, (p2.wl >> 2) - cs0, j - 1, r1.other - ds0), vi);
+              const int64_t wv = best_inner(vi, T.mm23, r1.label * 4 + (p2.wl & 3));
               if (!fin(wv)) continue;
               upd(af[8], wv + p2.cost + r1.cost + h + e23);
               TERM(5);

@@ -222,8 +222,10 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.Ihat = (int64_t *)take(ring * 8);
   d.IL = (int64_t *)take(ring * 8);
   d.Q = (int64_t *)take(ring * 6 * 8);
-  d.W = (int64_t *)take(ring * SD_WN * 8);
+  d.WB = (int64_t *)take(ring * 8);
   d.Af = (int64_t *)take(ring * SD_AN * 8);
+  d.Xc = (int64_t *)take((size_t)N * 4 * SD_XSPAN * SD_W * 8);
+  d.Yr = (int64_t *)take((size_t)N * 4 * SD_XSPAN * SD_W * 8);
   d.cand_cnt = (int32_t *)take(N * 4);
   d.cand_off = (int64_t *)take(N * 8);
   d.cand_c = (int32_t *)take((cap > 0 ? cap : 1) * 4);
