@@ -555,6 +555,11 @@ constexpr int IL_PAIRS = 375;
 // same position inside the codon at both ends, so the same layer types and
 // mostly the same branches); a block of 3 warps covers 3 * 32/G consecutive
 // layer pairs.
+// unroll factor of the fill's independent-iteration loops (more loads in flight)
+#ifndef SD_UNROLL
+#define SD_UNROLL 1
+#endif
+constexpr int kUnroll = SD_UNROLL;
 #ifndef SD_FILL_WARPS
 #define SD_FILL_WARPS 3  // warps per block for groups of 8 or 16 (a multiple of 3)
 #endif
@@ -660,6 +665,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   GapStage &GS = s_gap[threadIdx.x / G];
   {
     const int lmax = min(SD_GAPW - 1, g - 1);  // spans below g only (this span is not filled yet)
+#pragma unroll kUnroll
     for (int q = sub; q < SD_GAPW * SD_SLOTS; q += G) {
       const int l = q / SD_SLOTS, c = (q / SD_W) % SD_W, sn = q % SD_W;
       int64_t vl = SD_INF, vr = SD_INF;
@@ -679,10 +685,15 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     Bs[s] = SD_INF;
     PSs[s] = SD_INF;
   }
+  // the state pairs of this layer pair, and the most any group of the warp
+  // has: the slot loops run that many rounds (warp-uniform: the groups'
+  // shuffles need every lane), each group idling past its own count
+  const int nslot = active ? wa * wb : 0;
+  const int kslot = (int)__reduce_max_sync(FULL, (unsigned)nslot);
 #pragma unroll 1
-  for (int s = 0; s < SD_SLOTS; s++) {
-    const int sa = s / SD_W, sb = s % SD_W;
-    const bool ok = active && sa < wa && sb < wb;
+  for (int k = 0; k < kslot; k++) {
+    const bool ok = k < nslot;
+    const int sa = ok ? k / wb : 0, sb = ok ? k % wb : 0, s = sa * SD_W + sb;
     const int a = a0 + sa, b = b0 + sb;
     const int cell = ok ? F.cs(i, sa, j, sb) : 0;  // this state pair's full-table entry
     // gap cell (every thread of the group; at most a few in-edges)
@@ -753,7 +764,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       }
       B = settle(B);
       if (ok && sub == 0) D.Bv[cell] = B;
-      Bs[s] = B;
+      if (ok) Bs[s] = B;
     }
     // inner terms of this cell for the loops that will enclose it: the bulge
     // term WB (inner pair (a, b)) and the one-nucleotide-side factors X(a, b)
@@ -820,6 +831,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // 1 x n: u on layer lu, l2 = j + 2 - lu in [3, 29], inner span lu - 1 - i >= 5
         const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
         if (ulo <= uhi)
+#pragma unroll kUnroll
           for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
             const int lu = F.layer(u), us = u - F.ls(lu), l2 = j + 2 - lu;
             const int64_t h = GS.hr[j - lu][us * SD_W + sb];
@@ -841,6 +853,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // n x 1: w on layer lw, l1 = lw - i + 2 in [3, 29], inner span j - lw - 1 >= 5
         const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
         if (wlo <= whi)
+#pragma unroll kUnroll
           for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
             const int lw = F.layer(w), ws = w - F.ls(lw), l1 = lw - i + 2;
             const int64_t h = GS.hl[lw - i][ws * SD_W + sa];
@@ -923,6 +936,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 #pragma unroll
     for (int s = 0; s < SD_SLOTS; s++) lv[s] = SD_INF;
     if (active)
+#pragma unroll kUnroll
       for (int q = sub; q < IL_PAIRS; q += G) {
         const int pr = s_il[q];
         const int l1p = pr & 31, l2p = pr >> 5;
@@ -995,9 +1009,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   // Eq. (sparse2) for every slot: edge extensions, then splits at retained
   // candidates (the group splits the candidate list)
 #pragma unroll 1
-  for (int s = 0; s < SD_SLOTS; s++) {
-    const int sa = s / SD_W, sb = s % SD_W;
-    const bool ok = active && sa < wa && sb < wb;
+  for (int k = 0; k < kslot; k++) {
+    const bool ok = k < nslot;
+    const int sa = ok ? k / wb : 0, sb = ok ? k % wb : 0, s = sa * SD_W + sb;
     const int a = a0 + sa, b = b0 + sb;
     const int cell = ok ? F.cs(i, sa, j, sb) : 0;
     int64_t s2 = SD_INF;
@@ -1012,6 +1026,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         }
       const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
+#pragma unroll kUnroll
       for (int k = sub; k < cnt; k += G) {
         const int c = D.cand_c[off + k];
         const int lc = __ldg(&D.layer[c]);
