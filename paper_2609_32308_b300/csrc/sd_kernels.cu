@@ -303,6 +303,10 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
                                        unsigned long long &ops, const GapStage &GS) {
   const int g = ly - lx;
   const int nox = F.nout(x), niy = F.nin(y);
+  // (the 1x1 / 1x2 tables stay in global memory: a larger shared-memory
+  // carve-out would cost this kernel its L1 hit rate)
+  const int32_t(*I11)[6][16] = P.int11;
+  const int32_t(*I21)[6][64] = P.int21;
   const int lx1s = F.ls(lx + 1), ly1s = F.ls(ly - 1);
   // ---- hairpin (loop length L = g) ----
   if (g == 3 || g == 4 || g == 6) {
@@ -362,6 +366,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     const int r0 = F.ls(rlo), nr = F.ls(ly + 1) - r0;
     const int lhi = min(lx + SD_MAXTWO, ly - 5);  // layers of c on the left side
     const int c0 = lx1s, nl = lhi >= lx + 1 ? F.ls(lhi + 1) - c0 : 0;
+    int64_t bul = SD_INF;  // bulges l >= 2: inner part, AU(t) added once below
     for (int k = sub; k < nr + nl; k += G) {
       const bool right = k < nr;
       const int v = right ? r0 + k : c0 + (k - nr);
@@ -379,7 +384,8 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
         const int64_t w = ro(D.WB + rc);
         if (!fin(w)) continue;
-        upd6<COUNT>(qv, tm, w + h + fx(T.bulge[l]), 2, ops, [&](int t) { return T.au[t]; });
+        upd(bul, w + h + fx(T.bulge[l]));
+        TERM(2);
       } else {
         int64_t vv[6];
         const int vc = right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy);
@@ -394,6 +400,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         }
       }
     }
+    if (fin(bul)) upd6<COUNT>(qv, tm, bul, 0, ops, [&](int t) { return T.au[t]; });
   }
   // ---- 1 x 1 and 1 x 2: l1 = 1 (nucleotide p after the outer 5' end), l2 <= 2;
   // entries are the out-edges r1 of the inner pair's 3' end d (1 x n with
@@ -420,7 +427,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
             if (!fin(vv[ti])) continue;
             const int s = c_rev[ti];
             upd6<COUNT>(qv, tm, vv[ti] + base, 3, ops,
-                        [&](int t) { return P.int11[t][s][p * 4 + fR]; });
+                        [&](int t) { return I11[t][s][p * 4 + fR]; });
           }
         }
       } else {  // l2 == 2: explicit 2-edge right side
@@ -439,7 +446,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
               if (!fin(vv[ti])) continue;
               const int s = c_rev[ti];
               upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
-                          [&](int t) { return P.int21[t][s][p * 16 + fR * 4 + lR]; });
+                          [&](int t) { return I21[t][s][p * 16 + fR * 4 + lR]; });
             }
           }
         }
@@ -471,7 +478,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
             if (!fin(vv[ti])) continue;
             const int s = c_rev[ti];
             upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
-                        [&](int t) { return P.int21[s][t][r * 16 + fL * 4 + lL]; });
+                        [&](int t) { return I21[s][t][r * 16 + fL * 4 + lL]; });
           }
         }
       }
@@ -597,6 +604,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 #pragma unroll
     for (int q = 0; q < 5; q++)
       for (int k = threadIdx.x; k < cnt[q]; k += NT) dst[q][k] = src[q][k];
+
     for (int k = threadIdx.x; k < 27 * 27; k += NT) {
       const int l1p = k / 27, l2p = k % 27;
       if (l1p + l2p < 2 || l1p + l2p > SD_MAXTWO - 4) continue;
