@@ -640,6 +640,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d, int wclass) {
   d.Af = c.take<int64_t>(ring * SD_AN);
   d.Xc = c.take<int64_t>((size_t)N * 4 * SD_XSPAN * wclass);
   d.Yr = c.take<int64_t>((size_t)N * 4 * SD_XSPAN * wclass);
+  d.KR = c.take<int64_t>((size_t)SD_KRING * (n + 1) * wclass * wclass * SD_KM);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
   d.cand_cap = L.caps.empty() ? nullptr : c.take<int32_t>(N);

@@ -29,6 +29,8 @@
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
 #define SD_AN 12         // two-loop factor entries per cell slot (9 used, 96 bytes)
 #define SD_XSPAN 32      // spans kept per state in the 1 x n / n x 1 factor tables
+#define SD_KM 25         // internal-loop sizes kept per state pair for extension
+#define SD_KRING 4       // spans kept of them
 #define SD_MAX_NT 12000  // longest mRNA: keeps every table index inside int32
 
 // +infinity and the finiteness threshold of the fixed-point arithmetic.
@@ -152,6 +154,9 @@ struct SdDesign {
   //     over inner types of V(c,b) + mismatch1n(r after b, lL before c)
   // (N*4*32*W each, W the layer width of the kernel instance)
   int64_t *Xc, *Yr;
+  // SD_KRING*(n+1)*SLOTS*SD_KM best generic internal loops of each state pair
+  // by size m = l1'+l2' (0..24), asymmetry included (grown two spans up)
+  int64_t *KR;
   // SD_RING*(n+1)*SLOTS*SD_AN two-loop factors of each cell (a, b) for the
   // pairs closing one nucleotide outside it (read two spans up): [p] the
   // 1 x n loops (one unpaired nucleotide p entering a, >= 3 after b's side),

@@ -551,8 +551,6 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
   }
 }
 
-// (l1', l2') pairs of the generic internal loops, l1'+l2' in [2, 26]
-constexpr int IL_PAIRS = 375;
 
 // ---------------------------------------------------------------------------
 // the span kernel: a group of G threads (G = 8, 16 or 32) per layer pair
@@ -562,11 +560,7 @@ constexpr int IL_PAIRS = 375;
 // same position inside the codon at both ends, so the same layer types and
 // mostly the same branches); a block of 3 warps covers 3 * 32/G consecutive
 // layer pairs.
-// unroll factor of the fill's independent-iteration loops (more loads in flight)
-#ifndef SD_UNROLL
-#define SD_UNROLL 1
-#endif
-constexpr int kUnroll = SD_UNROLL;
+
 #ifndef SD_FILL_WARPS
 #define SD_FILL_WARPS 3  // warps per block for groups of 8 or 16 (a multiple of 3)
 #endif
@@ -593,8 +587,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
                 unsigned long long *ops_out) {
   constexpr int NT = FillShape<G>::threads;
   __shared__ SmallTables T;
-  __shared__ uint16_t s_il[IL_PAIRS];
-  __shared__ int32_t s_ile[IL_PAIRS];  // size and asymmetry energy of each (l1', l2')
   __shared__ GapStage s_gap[FillShape<G>::pairs];
   {
     const int32_t *src[] = {&Pp->stack[0][0], &Pp->mmH[0][0], &Pp->bulge[0], &Pp->au[0],
@@ -604,18 +596,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 #pragma unroll
     for (int q = 0; q < 5; q++)
       for (int k = threadIdx.x; k < cnt[q]; k += NT) dst[q][k] = src[q][k];
-
-    for (int k = threadIdx.x; k < 27 * 27; k += NT) {
-      const int l1p = k / 27, l2p = k % 27;
-      if (l1p + l2p < 2 || l1p + l2p > SD_MAXTWO - 4) continue;
-      // rank of (l1p, l2p) among the admissible pairs in row-major order
-      int r = 0;
-      for (int a = 0; a < l1p; a++) r += (SD_MAXTWO - 4 - a + 1) - (a < 2 ? 2 - a : 0);
-      r += l2p - (l1p < 2 ? 2 - l1p : 0);
-      s_il[r] = (uint16_t)(l1p | (l2p << 5));
-      const int dd = l1p > l2p ? l1p - l2p : l2p - l1p;
-      s_ile[r] = Pp->interior[l1p + l2p + 4] + min(Pp->maxninio, Pp->ninio * dd);
-    }
   }
   __syncthreads();
   unsigned long long ops = 0;
@@ -673,7 +653,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   GapStage &GS = s_gap[threadIdx.x / G];
   {
     const int lmax = min(SD_GAPW - 1, g - 1);  // spans below g only (this span is not filled yet)
-#pragma unroll kUnroll
     for (int q = sub; q < SD_GAPW * SD_SLOTS; q += G) {
       const int l = q / SD_SLOTS, c = (q / SD_W) % SD_W, sn = q % SD_W;
       int64_t vl = SD_INF, vr = SD_INF;
@@ -839,7 +818,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // 1 x n: u on layer lu, l2 = j + 2 - lu in [3, 29], inner span lu - 1 - i >= 5
         const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
         if (ulo <= uhi)
-#pragma unroll kUnroll
           for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
             const int lu = F.layer(u), us = u - F.ls(lu), l2 = j + 2 - lu;
             const int64_t h = GS.hr[j - lu][us * SD_W + sb];
@@ -861,7 +839,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // n x 1: w on layer lw, l1 = lw - i + 2 in [3, 29], inner span j - lw - 1 >= 5
         const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
         if (wlo <= whi)
-#pragma unroll kUnroll
           for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
             const int lw = F.layer(w), ws = w - F.ls(lw), l1 = lw - i + 2;
             const int64_t h = GS.hl[lw - i][ws * SD_W + sa];
@@ -936,83 +913,78 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       }
     }
   }
-  // IL: generic internal loops (l1 = l1'+2, l2 = l2'+2) around every slot of the
-  // layer pair at once: each inner cell (c,d) is read once for all slots, the
-  // gap values of both ends come from the staged vectors
-  if (g >= 9) {
-    int64_t lv[SD_SLOTS];
-#pragma unroll
-    for (int s = 0; s < SD_SLOTS; s++) lv[s] = SD_INF;
-    if (active)
-#pragma unroll kUnroll
-      for (int q = sub; q < IL_PAIRS; q += G) {
-        const int pr = s_il[q];
-        const int l1p = pr & 31, l2p = pr >> 5;
-        const int lc = i + l1p, ld = j - l2p;
-        if (ld - lc < 7) continue;
-        const int64_t e = fx(s_ile[q]);
-        const int rb = (((ld - lc) & (SD_RING - 1)) * (n + 1) + lc) * SD_SLOTS;
-        // slots beyond a layer's width have +inf staged gap values
-#if SD_W == 2
-#pragma unroll
-        for (int cs = 0; cs < 2; cs++) {
-          const int64_t hl0 = GS.hl[l1p][cs * 2], hl1 = GS.hl[l1p][cs * 2 + 1];
-          if (!fin(hl0) && !fin(hl1)) continue;
-#pragma unroll
-          for (int ds = 0; ds < 2; ds++) {
-            const int64_t hr0 = GS.hr[l2p][ds * 2], hr1 = GS.hr[l2p][ds * 2 + 1];
-            if (!fin(hr0) && !fin(hr1)) continue;
-            const int64_t v = ro(D.Ihat + rb + cs * 2 + ds);
-            if (!fin(v)) continue;
-            const int64_t ve = v + e;
-#pragma unroll
-            for (int s = 0; s < 4; s++) {
-              const int64_t h1 = (s >> 1) ? hl1 : hl0, h2 = (s & 1) ? hr1 : hr0;
-              if (fin(h1) && fin(h2)) {
-                upd(lv[s], h1 + ve + h2);
-                TERM(3);
+  // IL: generic internal loops (l1 = l1'+2, l2 = l2'+2 unpaired nucleotides,
+  // l1'+l2' = m in [2, 26]) below every state pair of the layer pair, by loop
+  // size.  K_m(x, y) is the best such loop inside (x, y) with l1'+l2' = m, its
+  // asymmetry term included: growing both unpaired sides by one nucleotide
+  // keeps |l1 - l2|, so a loop with both sides >= 1 is a loop of K_{m-2} of a
+  // state pair one nucleotide inside plus the two edges; a loop with one side
+  // empty is an inner mismatch cell (Ihat) on x's column or y's row plus the
+  // staged gap of the other side.  IL = min over m of K_m + the size term.
+  // K_0..K_24 are kept (ring of 4 spans) for the pairs two spans up.
+  __syncwarp();  // this layer pair's own Ihat (m = 0) was written above
+#pragma unroll 1
+  for (int k = 0; k < kslot; k++) {
+    const bool ok = k < nslot;
+    const int sa = ok ? k / wb : 0, sb = ok ? k % wb : 0, s = sa * SD_W + sb;
+    int64_t il = SD_INF;
+    if (ok && g >= 7) {
+      const int x = a0 + sa, y = b0 + sb;
+      int64_t *Kc = D.KR + ((int64_t)((g & 3) * (n + 1) + i) * SD_SLOTS + s) * SD_KM;
+      const int64_t *Kin = D.KR + (int64_t)(((g - 2) & 3) * (n + 1) + i + 1) * SD_SLOTS * SD_KM;
+      const int nox = F.nout(x), niy = F.nin(y);
+      for (int m = sub; m <= SD_MAXTWO - 4; m += G) {
+        int64_t km = SD_INF;
+        const int64_t asym = fx(min(T.maxninio, T.ninio * m));
+        // l1' = 0: the inner mismatch cell (x, b), b on layer j - m
+        const int lb = j - m;
+        if (lb - i >= 7)
+          for (int ds = 0; ds < F.w(lb); ds++) {
+            const int64_t h = m == 0 ? (ds == sb ? 0 : SD_INF) : GS.hr[m][ds * SD_W + sb];
+            if (!fin(h)) continue;
+            const int r = F.rs(i, sa, lb, ds);
+            const int64_t v = m == 0 ? D.Ihat[r] : ro(D.Ihat + r);
+            if (fin(v)) {
+              upd(km, v + h + asym);
+              TERM(2);
+            }
+          }
+        // l2' = 0, l1' = m >= 1: the inner mismatch cell (a, y), a on layer i + m
+        const int la = i + m;
+        if (m >= 1 && j - la >= 7)
+          for (int cs = 0; cs < F.w(la); cs++) {
+            const int64_t h = GS.hl[m][cs * SD_W + sa];
+            if (!fin(h)) continue;
+            const int64_t v = ro(D.Ihat + F.rs(la, cs, j, sb));
+            if (fin(v)) {
+              upd(km, v + h + asym);
+              TERM(2);
+            }
+          }
+        // both sides >= 1: K_{m-2} of the state pair (x', y') one nucleotide inside
+        if (m >= 2 && g >= 9)
+          for (int a2 = 0; a2 < nox; a2++) {
+            const SdEdge e1 = F.out(x, a2);
+            for (int b2 = 0; b2 < niy; b2++) {
+              const SdEdge e2 = F.in(y, b2);
+              const int64_t kv =
+                  ro(Kin + ((e1.other - i1s) * SD_W + (e2.other - js)) * SD_KM + m - 2);
+              if (fin(kv)) {
+                upd(km, kv + e1.cost + e2.cost);
+                TERM(2);
               }
             }
           }
+        km = settle(km);
+        if (m < SD_KM) Kc[m] = km;
+        if (m >= 2 && fin(km)) {
+          upd(il, km + fx(T.interior[m + 4]));
+          TERM(1);
         }
-#else
-#pragma unroll
-        for (int cs = 0; cs < SD_W; cs++) {
-          bool anyl = false;
-#pragma unroll
-          for (int sa = 0; sa < SD_W; sa++) anyl |= fin(GS.hl[l1p][cs * SD_W + sa]);
-          if (!anyl) continue;
-#pragma unroll
-          for (int ds = 0; ds < SD_W; ds++) {
-            bool anyr = false;
-#pragma unroll
-            for (int sb = 0; sb < SD_W; sb++) anyr |= fin(GS.hr[l2p][ds * SD_W + sb]);
-            if (!anyr) continue;
-            const int64_t v = ro(D.Ihat + rb + cs * SD_W + ds);
-            if (!fin(v)) continue;
-            const int64_t ve = v + e;
-#pragma unroll
-            for (int s = 0; s < SD_SLOTS; s++) {
-              const int64_t h1 = GS.hl[l1p][cs * SD_W + s / SD_W];
-              const int64_t h2 = GS.hr[l2p][ds * SD_W + s % SD_W];
-              if (fin(h1) && fin(h2)) {
-                upd(lv[s], h1 + ve + h2);
-                TERM(3);
-              }
-            }
-          }
-        }
-#endif
       }
-#pragma unroll
-    for (int s = 0; s < SD_SLOTS; s++) {
-      seg_min<G>(lv[s]);
-      if (active && s / SD_W < wa && s % SD_W < wb && sub == s % G) D.IL[rcell + s] = settle(lv[s]);
     }
-  } else if (active && sub == 0) {
-#pragma unroll
-    for (int s = 0; s < SD_SLOTS; s++)
-      if (s / SD_W < wa && s % SD_W < wb) D.IL[rcell + s] = SD_INF;
+    seg_min<G>(il);
+    if (ok && sub == 0) D.IL[rcell + s] = settle(il);
   }
   // Eq. (sparse2) for every slot: edge extensions, then splits at retained
   // candidates (the group splits the candidate list)
@@ -1034,7 +1006,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         }
       const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
-#pragma unroll kUnroll
       for (int k = sub; k < cnt; k += G) {
         const int c = D.cand_c[off + k];
         const int lc = __ldg(&D.layer[c]);
