@@ -98,7 +98,9 @@ int sd_load_energy(const char *path_or_null, uint64_t synthetic_seed, sd_energy 
 int sd_energy_save(const sd_energy *e, const char *path);
 void sd_energy_free(sd_energy *e);
 
-/* Exact design of one protein (Sec. 3, Eq. 1).
+/* Exact design of one protein (Sec. 3, Eq. 1: the minimum over the synonymous
+ * mRNAs r of the protein of MFE(r) + 100 lambda C(r), with C(r) the sum over
+ * codons of -ln w(codon), and an MFE structure of the minimising r).
  *   protein       one-letter amino acids, optional '*' as the last symbol only
  *                 (an explicit stop adds a codon position; none is implied);
  *                 may be empty; at most 4000 codon positions (12,000 nt).
@@ -107,15 +109,21 @@ void sd_energy_free(sd_energy *e);
  *                 the protein (and '*') the maximum over its codons must be 1.
  *   lambda        >= 0, kcal/mol.
  * Fills *out (caller-owned struct; buffers freed by sd_result_free).
- * Returns SD_OK or SD_EINVAL / SD_ERANGE / SD_ENOMEM / SD_ECUDA / SD_EINTERNAL. */
+ * Returns SD_OK or SD_EINVAL / SD_ERANGE / SD_ENOMEM / SD_ECUDA / SD_EINTERNAL,
+ * or SD_EINFEASIBLE when the design language is empty (no complete mRNA; a
+ * protein alone always has one, forbidden motifs can remove them all). */
 int sd_design(const sd_energy *energy, const char *protein, const double *codon_weights,
               double lambda, sd_result *out);
 
-/* Exact designs of many proteins in one batched launch sequence.
+/* Exact designs of many proteins in one batched launch sequence: Sec. 3, Eq. 1
+ * applied to every item independently (one lattice, codon weights and lambda
+ * per item; the items share the launches of the span wavefront, Sec. 5).
  *   proteins[count], codon_weights (count*64 values, or 64 if weights_shared),
  *   lambdas[count]; outs[count] and status[count] are caller-owned arrays.
- * One failing item does not stop the others; status[k] holds its code.
- * Returns SD_OK if the batch ran (check status[]), else an error code. */
+ * One failing item does not stop the others; status[k] holds its code (any
+ * code sd_design returns, SD_EINFEASIBLE included).
+ * Returns SD_OK if the batch ran (check status[]), else SD_EINVAL (NULL or
+ * negative arguments), SD_ENOMEM, SD_ECUDA or SD_EINTERNAL. */
 int sd_design_batch(const sd_energy *energy, int count, const char *const *proteins,
                     const double *codon_weights, int weights_shared, const double *lambdas,
                     sd_result *outs, int *status);
@@ -196,7 +204,8 @@ int sd_inverse_lambda(const sd_energy *energy, const char *protein, const double
  * All calls share the scratch: calls that overlap on the GPU (two host
  * threads, or work still in flight) race and must be serialised.
  * Runs on the legacy default stream and returns when the design is complete.
- * Returns SD_OK, SD_EINVAL, SD_ERANGE, SD_ESIZE, SD_ECUDA or SD_EINTERNAL. */
+ * Returns SD_OK, SD_EINVAL, SD_ERANGE, SD_ESIZE, SD_ECUDA, SD_EINTERNAL or
+ * SD_EINFEASIBLE (empty design language, as for sd_design). */
 int sd_design_noalloc(const sd_energy *energy, const char *protein, const double *codon_weights,
                       double lambda, sd_result *out);
 

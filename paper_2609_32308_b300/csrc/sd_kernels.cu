@@ -170,6 +170,33 @@ __device__ __forceinline__ void seg_min(int64_t &v) {
   for (int o = G / 2; o > 0; o >>= 1) upd(v, __shfl_xor_sync(FULL, v, o));
 }
 
+// Minimum of eight values across the G >= 8 threads of a group, each thread
+// ending with one of them: recursive halving (every exchange step trades half
+// of the values still held), so the result of value (sub & 7) lands in thread
+// sub after 4 + 2 + 1 exchanges instead of 8 * log2(G).
+template <int G>
+__device__ __forceinline__ int64_t seg_min8(const int64_t *x, int sub) {
+  const bool b2 = (sub >> 2) & 1, b1 = (sub >> 1) & 1, b0 = sub & 1;
+  int64_t y[4], z[2];
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const int64_t r = __shfl_xor_sync(FULL, b2 ? x[k] : x[k + 4], 4);
+    y[k] = b2 ? x[k + 4] : x[k];
+    upd(y[k], r);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; k++) {
+    const int64_t r = __shfl_xor_sync(FULL, b1 ? y[k] : y[k + 2], 2);
+    z[k] = b1 ? y[k + 2] : y[k];
+    upd(z[k], r);
+  }
+  int64_t v = b0 ? z[1] : z[0];
+  upd(v, __shfl_xor_sync(FULL, b0 ? z[0] : z[1], 1));
+#pragma unroll
+  for (int o = 8; o < G; o <<= 1) upd(v, __shfl_xor_sync(FULL, v, o));
+  return v;
+}
+
 // Design view for the fill: hot pointers in registers, 32-bit index math
 // (sizes are limited to n <= 12000 nucleotides on the host).
 struct Fv {
@@ -241,6 +268,33 @@ struct Fv {
 constexpr int SD_GAPW = SD_MAXTWO + 1;
 struct GapStage {
   int64_t hl[SD_GAPW][SD_SLOTS], hr[SD_GAPW][SD_SLOTS];
+};
+
+// The states of the layers lo..hi as entries k = 0 .. cnt-1, each a (layer,
+// slot) pair.  With narrow layers every (layer, slot) pair is an entry and
+// the caller's staged gap value, +inf past the width of its layer, rejects
+// the empty slots: no lattice lookup per entry.  Wide layers walk the states.
+struct LayerRange {
+  int lo, base, cnt;
+  __device__ __forceinline__ LayerRange(const Fv &F, int lo_, int hi) : lo(lo_), base(0), cnt(0) {
+    if (hi < lo) return;
+    if (SD_W == 2) {
+      cnt = (hi - lo + 1) * SD_W;
+    } else {
+      base = F.ls(lo);
+      cnt = F.ls(hi + 1) - base;
+    }
+  }
+  __device__ __forceinline__ void at(const Fv &F, int k, int &l, int &s) const {
+    if (SD_W == 2) {
+      l = lo + k / SD_W;
+      s = k % SD_W;
+    } else {
+      const int v = base + k;
+      l = F.layer(v);
+      s = v - F.ls(l);
+    }
+  }
 };
 
 // minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
@@ -362,23 +416,19 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
   if (g < 5) return;
   // ---- stack and bulges: right side (l1 = 0, l2 = l >= 0), left side (l2 = 0, l1 = l >= 1) ----
   {
-    const int rlo = max(ly - SD_MAXTWO, lx + 5);  // layers of d on the right side
-    const int r0 = F.ls(rlo), nr = F.ls(ly + 1) - r0;
-    const int lhi = min(lx + SD_MAXTWO, ly - 5);  // layers of c on the left side
-    const int c0 = lx1s, nl = lhi >= lx + 1 ? F.ls(lhi + 1) - c0 : 0;
+    // layers of d on the right side, of c on the left side
+    const LayerRange R(F, max(ly - SD_MAXTWO, lx + 5), ly), Lf(F, lx + 1, min(lx + SD_MAXTWO, ly - 5));
+    const int nr = R.cnt;
     int64_t bul = SD_INF;  // bulges l >= 2: inner part, AU(t) added once below
-    for (int k = sub; k < nr + nl; k += G) {
+    for (int k = sub; k < nr + Lf.cnt; k += G) {
       const bool right = k < nr;
-      const int v = right ? r0 + k : c0 + (k - nr);
-      const int lv = F.layer(v), sv = v - F.ls(lv);
+      int lv, sv;
+      if (right) R.at(F, k, lv, sv);
+      else Lf.at(F, k - nr, lv, sv);
       const int l = right ? ly - lv : lv - lx;
-      int64_t h = 0;
-      if (l > 0) {
-        h = right ? GS.hr[l][sv * SD_W + sy] : GS.hl[l][sv * SD_W + sx];
-        if (!fin(h)) continue;
-      } else if (sv != sy) {
-        continue;
-      }
+      // staged gap (l = 0: 0 on y itself, +inf elsewhere)
+      const int64_t h = right ? GS.hr[l][sv * SD_W + sy] : GS.hl[l][sv * SD_W + sx];
+      if (!fin(h)) continue;
       if (l >= 2) {
         // bulge: bulge[l] + AU(t) + AU(inner); best inner type from WB
         const int rc = right ? F.rs(lx, sx, lv, sv) : F.rs(lv, sv, ly, sy);
@@ -408,12 +458,17 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
   {
     const int lc = lx + 1;
     const int dlo = max(lx + 6, ly - 2), dhi = ly - 1;
-    const int k0 = dlo <= dhi ? F.fo_off[F.ls(dlo)] : 0;
+    // out-edges of the states of layers dlo..dhi (at most ly-2 and ly-1) in
+    // state order: the edges of layer dhi start at kb
+    const int dlos = F.ls(dlo), dhis = F.ls(dhi);
+    const int k0 = dlo <= dhi ? F.fo_off[dlos] : 0;
+    const int kb = dlo <= dhi ? F.fo_off[dhis] : 0;
     const int k1 = dlo <= dhi ? F.fo_off[F.ls(dhi + 1)] : 0;
     for (int k = k0 + sub; k < k1; k += G) {
       const SdFlatEdge r1 = F.fo[k];
       const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
-      const int ld = F.layer(d), ds = d - F.ls(ld), l2 = ly - ld;
+      const bool hi = k >= kb;
+      const int ld = hi ? dhi : dlo, ds = d - (hi ? dhis : dlos), l2 = ly - ld;
       if (l2 == 1) {
         if (u != y) continue;
         for (int a = 0; a < nox; a++) {
@@ -458,11 +513,12 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
   // from Af) ----
   if (g >= 8) {
     const int ld = ly - 1, lc = lx + 2;
-    const int k0 = F.fi_off[F.ls(lc)], k1 = F.fi_off[F.ls(lc + 1)];
+    const int lcs = F.ls(lc);
+    const int k0 = F.fi_off[lcs], k1 = F.fi_off[F.ls(lc + 1)];
     for (int k = k0 + sub; k < k1; k += G) {
       const SdFlatEdge p2 = F.fi[k];
       const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
-      const int cs = c - F.ls(lc);
+      const int cs = c - lcs;
       for (int b = 0; b < niy; b++) {
         const SdEdge er = F.in(y, b);
         const int r = er.label, ds = er.other - ly1s;
@@ -899,17 +955,12 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         }
       }
-#pragma unroll
-      for (int q = 0; q < 9; q++) seg_min<G>(af[q]);
+      const int64_t af8 = seg_min8<G>(af, sub);
+      seg_min<G>(af[8]);
       if (ok) {
         int64_t *Afc = D.Af + (int64_t)(rcell + s) * SD_AN;
-        for (int q = sub; q < 9; q += G) {
-          int64_t v = SD_INF;
-#pragma unroll
-          for (int t = 0; t < 9; t++)
-            if (t == q) v = af[t];
-          Afc[q] = settle(v);
-        }
+        if (sub < 8) Afc[sub] = settle(af8);
+        if (sub == 0) Afc[8] = settle(af[8]);
       }
     }
   }
@@ -939,8 +990,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // l1' = 0: the inner mismatch cell (x, b), b on layer j - m
         const int lb = j - m;
         if (lb - i >= 7)
-          for (int ds = 0; ds < F.w(lb); ds++) {
-            const int64_t h = m == 0 ? (ds == sb ? 0 : SD_INF) : GS.hr[m][ds * SD_W + sb];
+          for (int ds = 0; ds < (SD_W == 2 ? SD_W : F.w(lb)); ds++) {
+            const int64_t h = GS.hr[m][ds * SD_W + sb];  // +inf past the width
             if (!fin(h)) continue;
             const int r = F.rs(i, sa, lb, ds);
             const int64_t v = m == 0 ? D.Ihat[r] : ro(D.Ihat + r);
@@ -952,8 +1003,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // l2' = 0, l1' = m >= 1: the inner mismatch cell (a, y), a on layer i + m
         const int la = i + m;
         if (m >= 1 && j - la >= 7)
-          for (int cs = 0; cs < F.w(la); cs++) {
-            const int64_t h = GS.hl[m][cs * SD_W + sa];
+          for (int cs = 0; cs < (SD_W == 2 ? SD_W : F.w(la)); cs++) {
+            const int64_t h = GS.hl[m][cs * SD_W + sa];  // +inf past the width
             if (!fin(h)) continue;
             const int64_t v = ro(D.Ihat + F.rs(la, cs, j, sb));
             if (fin(v)) {
@@ -1090,11 +1141,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 #pragma unroll
       for (int t = 0; t < 6; t++) qv[t] = SD_INF;
       if (tm) q_slot<G, COUNT>(F, D, P, T, sub, a0 + sa, b0 + sb, i, sa, j, sb, tm, qv, ops, GS);
-#pragma unroll
-      for (int t = 0; t < 6; t++) {
-        if (tm) seg_min<G>(qv[t]);
-        if (ok && sub == t % G) D.Q[(int64_t)(rcell + s) * 6 + t] = settle(qv[t]);
-      }
+      const int64_t q8[8] = {qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], SD_INF, SD_INF};
+      const int64_t qt = seg_min8<G>(q8, sub);  // type sub & 7
+      if (ok && sub < 6) D.Q[(int64_t)(rcell + s) * 6 + sub] = settle(qt);
     }
     if (COUNT && active && ops) atomicAdd(&ops_out[dsel], ops);
     return;
@@ -1176,11 +1225,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
                        ops, s_gap[(threadIdx.x >> 5) * NGW + go_k]);
     }
     const int o_rcell = ((g & (SD_RING - 1)) * (Do.n + 1) + o_i) * SD_SLOTS;
-#pragma unroll
-    for (int t = 0; t < 6; t++) {
-      if (__any_sync(FULL, (tm_k >> t) & 1)) seg_min<G>(qv[t]);
-      if (tm_k && sub == t % G) Do.Q[(int64_t)(o_rcell + s_k) * 6 + t] = settle(qv[t]);
-    }
+    const int64_t q8[8] = {qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], SD_INF, SD_INF};
+    const int64_t qt = seg_min8<G>(q8, sub);  // type sub & 7
+    if (tm_k && sub < 6) Do.Q[(int64_t)(o_rcell + s_k) * 6 + sub] = settle(qt);
     if (COUNT && tm_k && ops) atomicAdd(&ops_out[o_dsel], ops);
     ops = 0;
   }

@@ -191,10 +191,26 @@ def main():
     ap.add_argument("--energy-seed", type=int, default=1)
     ap.add_argument("--seed", type=int, default=7)
     ap.add_argument("--report", default=None, help="write a JSON summary here")
+    ap.add_argument("--eval-only", action="store_true",
+                    help="evaluate the parameters in --out on the held-out designs again "
+                         "(no labels, no training); keeps the training figures of --report")
     args = ap.parse_args()
     energy = Energy(None, args.energy_seed)  # the library's seeded synthetic set
     items = corpus(args.train + args.held_out, args.seed, hi=args.hi)
     tr, ho = items[:args.train], items[args.train:]
+    if args.eval_only:
+        prev = {}
+        if args.report and os.path.exists(args.report):
+            with open(args.report) as fh:
+                prev = json.load(fh)
+        t0 = time.time()
+        prev.update(evaluate(energy, load(args.out), ho, margin=args.margin))
+        prev.update({"eval_s": time.time() - t0, "margin": args.margin})
+        print(json.dumps(prev))
+        if args.report:
+            with open(args.report, "w") as fh:
+                json.dump(prev, fh, indent=1)
+        return
     t0 = time.time()
     counts = retention_labels(energy, tr)
     t_label = time.time() - t0

@@ -218,3 +218,32 @@ def test_shipped_predictor_on_unseen_proteins(sd, E1):
     assert ev["regrows"] <= 2, ev
     assert ev["room_ratio"] < 0.5, ev
     assert ev["room_pred"] >= ev["retained"]
+
+
+def test_presized_plan_same_speed(sd, E1):
+    """Presizing the candidate lists buys device memory, not time: with the
+    shipped predictor the fill of a presized plan takes no longer than the
+    worst-case plan's (5% slack for timing noise), every design identical and
+    the reserved candidate room and device bytes smaller."""
+    from paper_2609_32308_b300 import retention
+    pred = retention.load()
+    items = retention.corpus(8, seed=555, lo=250, hi=500)
+    args = ([p for p, _, _ in items], np.stack([w for _, w, _ in items]),
+            [lam for _, _, lam in items])
+    fill, keys, room, nbytes = {}, {}, {}, {}
+    for name, kw in (("plain", {}), ("pred", {"predictor": pred, "margin": 2.0})):
+        p = sd.Plan(E1, *args, **kw)
+        try:
+            p.set_timing(True)
+            ts = []
+            for _ in range(3):
+                p.run()
+                ts.append(p.phase_times()[0])
+            fill[name] = min(ts)
+            keys[name] = [_design_keys(r) for r in p.results()]
+            room[name], nbytes[name] = p.candidate_room, p.device_bytes
+        finally:
+            p.free()
+    assert keys["pred"] == keys["plain"]
+    assert room["pred"] < room["plain"] and nbytes["pred"] < nbytes["plain"]
+    assert fill["pred"] <= 1.05 * fill["plain"] + 1.0, fill
