@@ -134,8 +134,8 @@ __device__ __forceinline__ int hairpin_generic_e(const SdParams &P, const int32_
 
 // hairpin energy of the complete hairpin: pair t, loop labels packed 2 bits
 // each with the first loop label most significant
-__device__ int hairpin_seq_e(const SdParams &P, const int32_t *hp_len, int t, uint32_t labs,
-                             int L) {
+__device__ __noinline__ int hairpin_seq_e(const SdParams &P, const int32_t *hp_len, int t,
+                                          uint32_t labs, int L) {
   const int s = L == 3 ? 0 : L == 4 ? 1 : L == 6 ? 2 : -1;
   const int first = (labs >> (2 * (L - 1))) & 3, last = labs & 3;
   if (s >= 0) {
@@ -237,21 +237,10 @@ struct Fv {
   __device__ __forceinline__ int nin(int v) const { return in_[v]; }
   __device__ __forceinline__ SdEdge out(int v, int k) const { return oe[v * SD_MAXOUT + k]; }
   __device__ __forceinline__ SdEdge in(int v, int k) const { return ie[v * maxin + k]; }
-  // V of a cell of an earlier span (read-only path) ...
+  // V of a cell of an earlier span (read-only path)
   __device__ __forceinline__ void v6(int idx, int64_t (&vv)[6]) const {
     const longlong2 *p = reinterpret_cast<const longlong2 *>(V + (int64_t)idx * 6);
     const longlong2 a = ro(p), b = ro(p + 1), c = ro(p + 2);
-    vv[0] = a.x;
-    vv[1] = a.y;
-    vv[2] = b.x;
-    vv[3] = b.y;
-    vv[4] = c.x;
-    vv[5] = c.y;
-  }
-  // ... or of the current span (written by this launch)
-  __device__ __forceinline__ void v6_cur(int idx, int64_t (&vv)[6]) const {
-    const longlong2 *p = reinterpret_cast<const longlong2 *>(V + (int64_t)idx * 6);
-    const longlong2 a = p[0], b = p[1], c = p[2];
     vv[0] = a.x;
     vv[1] = a.y;
     vv[2] = b.x;
@@ -297,6 +286,10 @@ struct LayerRange {
   }
 };
 
+// the type of the same pair read from the other strand (AU <-> UA, CG <-> GC,
+// GU <-> UG)
+__device__ __forceinline__ int rev_type(int t) { return t < 4 ? 3 - t : 9 - t; }
+
 // minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
 __device__ __forceinline__ int64_t best_inner(const int64_t (&vv)[6], const int32_t (*tab)[16],
                                               int idx) {
@@ -304,15 +297,6 @@ __device__ __forceinline__ int64_t best_inner(const int64_t (&vv)[6], const int3
 #pragma unroll
   for (int ti = 0; ti < 6; ti++)
     if (fin(vv[ti])) upd(bv, vv[ti] + fx(tab[c_rev[ti]][idx]));
-  return bv;
-}
-
-// minimum over the inner pair types of vv[ti] + AU(rev ti)
-__device__ __forceinline__ int64_t best_au(const int64_t (&vv)[6], const int32_t *au) {
-  int64_t bv = SD_INF;
-#pragma unroll
-  for (int ti = 0; ti < 6; ti++)
-    if (fin(vv[ti])) upd(bv, vv[ti] + fx(au[c_rev[ti]]));
   return bv;
 }
 
@@ -404,6 +388,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     }
   } else if (g >= 5) {
     const int64_t he = fx(__ldg(&D.hp_len[g]));
+#pragma unroll 1
     for (int k = sub; k < nox * niy; k += G) {
       const int a = k / niy, b = k - a * niy;
       const SdEdge e1 = F.out(x, a), e2 = F.in(y, b);
@@ -420,6 +405,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     const LayerRange R(F, max(ly - SD_MAXTWO, lx + 5), ly), Lf(F, lx + 1, min(lx + SD_MAXTWO, ly - 5));
     const int nr = R.cnt;
     int64_t bul = SD_INF;  // bulges l >= 2: inner part, AU(t) added once below
+#pragma unroll 1
     for (int k = sub; k < nr + Lf.cnt; k += G) {
       const bool right = k < nr;
       int lv, sv;
@@ -437,16 +423,15 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         upd(bul, w + h + fx(T.bulge[l]));
         TERM(2);
       } else {
-        int64_t vv[6];
         const int vc = right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy);
-        if (l == 0) F.v6_cur(vc, vv);
-        else F.v6(vc, vv);
+        const int64_t *vr = F.V + (int64_t)vc * 6;
         const int64_t e1 = h + fx(l == 1 ? T.bulge[1] : 0);
-#pragma unroll
+#pragma unroll 1
         for (int ti = 0; ti < 6; ti++) {
-          if (!fin(vv[ti])) continue;
-          const int s = c_rev[ti];
-          upd6<COUNT>(qv, tm, vv[ti] + e1, 2, ops, [&](int t) { return T.stack[t][s]; });
+          const int64_t v = l == 0 ? vr[ti] : ro(vr + ti);
+          if (!fin(v)) continue;
+          const int s = rev_type(ti);
+          upd6<COUNT>(qv, tm, v + e1, 2, ops, [&](int t) { return T.stack[t][s]; });
         }
       }
     }
@@ -464,6 +449,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     const int k0 = dlo <= dhi ? F.fo_off[dlos] : 0;
     const int kb = dlo <= dhi ? F.fo_off[dhis] : 0;
     const int k1 = dlo <= dhi ? F.fo_off[F.ls(dhi + 1)] : 0;
+#pragma unroll 1
     for (int k = k0 + sub; k < k1; k += G) {
       const SdFlatEdge r1 = F.fo[k];
       const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
@@ -471,36 +457,38 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
       const int ld = hi ? dhi : dlo, ds = d - (hi ? dhis : dlos), l2 = ly - ld;
       if (l2 == 1) {
         if (u != y) continue;
+#pragma unroll 1
         for (int a = 0; a < nox; a++) {
           const SdEdge ec = F.out(x, a);
           const int p = ec.label, cs = ec.other - lx1s;
-          int64_t vv[6];
-          F.v6(F.cs(lc, cs, ld, ds), vv);
+          const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
           const int64_t base = ec.cost + r1.cost;
-#pragma unroll
+#pragma unroll 1
           for (int ti = 0; ti < 6; ti++) {
-            if (!fin(vv[ti])) continue;
-            const int s = c_rev[ti];
-            upd6<COUNT>(qv, tm, vv[ti] + base, 3, ops,
-                        [&](int t) { return I11[t][s][p * 4 + fR]; });
+            const int64_t v = ro(vr + ti);
+            if (!fin(v)) continue;
+            const int s = rev_type(ti);
+            upd6<COUNT>(qv, tm, v + base, 3, ops, [&](int t) { return I11[t][s][p * 4 + fR]; });
           }
         }
       } else {  // l2 == 2: explicit 2-edge right side
+#pragma unroll 1
         for (int b2 = 0; b2 < F.nout(u); b2++) {
           const SdEdge r2 = F.out(u, b2);
           if (r2.other != y) continue;
           const int lR = r2.label;
+#pragma unroll 1
           for (int a = 0; a < nox; a++) {
             const SdEdge ec = F.out(x, a);
             const int p = ec.label, cs = ec.other - lx1s;
-            int64_t vv[6];
-            F.v6(F.cs(lc, cs, ld, ds), vv);
+            const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
             const int64_t base = ec.cost + r1.cost + r2.cost;
-#pragma unroll
+#pragma unroll 1
             for (int ti = 0; ti < 6; ti++) {
-              if (!fin(vv[ti])) continue;
-              const int s = c_rev[ti];
-              upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
+              const int64_t v = ro(vr + ti);
+              if (!fin(v)) continue;
+              const int s = rev_type(ti);
+              upd6<COUNT>(qv, tm, v + base, 4, ops,
                           [&](int t) { return I21[t][s][p * 16 + fR * 4 + lR]; });
             }
           }
@@ -515,25 +503,28 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     const int ld = ly - 1, lc = lx + 2;
     const int lcs = F.ls(lc);
     const int k0 = F.fi_off[lcs], k1 = F.fi_off[F.ls(lc + 1)];
+#pragma unroll 1
     for (int k = k0 + sub; k < k1; k += G) {
       const SdFlatEdge p2 = F.fi[k];
       const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
       const int cs = c - lcs;
+#pragma unroll 1
       for (int b = 0; b < niy; b++) {
         const SdEdge er = F.in(y, b);
         const int r = er.label, ds = er.other - ly1s;
-        int64_t vv[6];
-        F.v6(F.cs(lc, cs, ld, ds), vv);
+        const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
+#pragma unroll 1
         for (int a = 0; a < nox; a++) {
           const SdEdge p1 = F.out(x, a);
           if (p1.other != w) continue;
           const int fL = p1.label;
           const int64_t base = er.cost + p1.cost + p2.cost;
-#pragma unroll
+#pragma unroll 1
           for (int ti = 0; ti < 6; ti++) {
-            if (!fin(vv[ti])) continue;
-            const int s = c_rev[ti];
-            upd6<COUNT>(qv, tm, vv[ti] + base, 4, ops,
+            const int64_t v = ro(vr + ti);
+            if (!fin(v)) continue;
+            const int s = rev_type(ti);
+            upd6<COUNT>(qv, tm, v + base, 4, ops,
                         [&](int t) { return I21[s][t][r * 16 + fL * 4 + lL]; });
           }
         }
@@ -547,30 +538,38 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     const int lcs = F.ls(lc), lds = F.ls(ld), lc1s = F.ls(lc - 1), ld1s = F.ls(ld + 1);
     const int pi0 = F.fi_off[lcs], npi = F.fi_off[F.ls(lc + 1)] - pi0;
     const int ro0 = F.fo_off[lds], nro = F.fo_off[F.ls(ld + 1)] - ro0;
+#pragma unroll 1
     for (int k = sub; k < npi * nro; k += G) {
       const int kp = k / nro, kr = k - kp * nro;
       const SdFlatEdge p2 = F.fi[pi0 + kp], r1 = F.fo[ro0 + kr];
       const int cs = p2.v - lcs, ds = r1.v - lds;
       const int w = p2.wl >> 2, lL = p2.wl & 3, u = r1.wl >> 2, fR = r1.wl & 3;
-      int64_t vv[6];
-      F.v6(F.cs(lc, cs, ld, ds), vv);
-      if (!(fin(vv[0]) || fin(vv[1]) || fin(vv[2]) || fin(vv[3]) || fin(vv[4]) || fin(vv[5])))
-        continue;
+      const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
+      int fm = 0;  // the inner types with a finite V
+      {
+        int64_t vv[6];
+        F.v6(F.cs(lc, cs, ld, ds), vv);
+#pragma unroll
+        for (int ti = 0; ti < 6; ti++) fm |= (int)fin(vv[ti]) << ti;
+      }
+      if (!fm) continue;
+#pragma unroll 1
       for (int a = 0; a < nox; a++) {
         const SdEdge p1 = F.out(x, a);
         const int64_t hl = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lc1s);
         if (!fin(hl)) continue;
+#pragma unroll 1
         for (int b2 = 0; b2 < niy; b2++) {
           const SdEdge r2 = F.in(y, b2);
           const int64_t hr = F.Hh(ld + 1, u - ld1s, ly - 1, r2.other - ly1s);
           if (!fin(hr)) continue;
           const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
           const int idx = p1.label * 64 + lL * 16 + fR * 4 + r2.label;
-#pragma unroll
+#pragma unroll 1
           for (int ti = 0; ti < 6; ti++) {
-            if (!fin(vv[ti])) continue;
-            const int s = c_rev[ti];
-            upd6<COUNT>(qv, tm, vv[ti] + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
+            if (!((fm >> ti) & 1)) continue;
+            const int s = rev_type(ti);
+            upd6<COUNT>(qv, tm, ro(vr + ti) + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
           }
         }
       }
@@ -581,6 +580,7 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
   // cell's tables two spans below: generic internal loops (IL), 1 x n and n x 1
   // with the long side >= 3 and 2x3 / 3x2 (the factors Af) ----
   if (g >= 9)
+#pragma unroll 1
     for (int k = sub; k < nox * niy; k += G) {
       const int a = k / niy, b = k - a * niy;
       const SdEdge e1 = F.out(x, a), e2 = F.in(y, b);
@@ -739,26 +739,29 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const int sa = ok ? k / wb : 0, sb = ok ? k % wb : 0, s = sa * SD_W + sb;
     const int a = a0 + sa, b = b0 + sb;
     const int cell = ok ? F.cs(i, sa, j, sb) : 0;  // this state pair's full-table entry
-    // gap cell (every thread of the group; at most a few in-edges)
-    if (ok) {
+    // gap cell: thread k of the group takes in-edge k of b
+    {
       int64_t hv = SD_INF;
-      const int nib = F.nin(b);
-#pragma unroll
-      for (int k = 0; k < (SD_W == 2 ? SD_MAXIN : SD_MAXIN_WIDE); k++) {
-        if (k >= nib) break;
-        const SdEdge e = F.in(b, k);
-        const int64_t hp = g == 1 ? (e.other == a ? 0 : SD_INF) : ro(F.H + F.cs(i, sa, j - 1, e.other - js));
-        if (!fin(hp)) continue;
-        upd(hv, hp + e.cost);
-        TERM(1);
+      if (ok) {
+        const int nib = F.nin(b);
+#pragma unroll 1
+        for (int k = sub; k < nib; k += G) {
+          const SdEdge e = F.in(b, k);
+          const int64_t hp = g == 1 ? (e.other == a ? 0 : SD_INF) : ro(F.H + F.cs(i, sa, j - 1, e.other - js));
+          if (!fin(hp)) continue;
+          upd(hv, hp + e.cost);
+          TERM(1);
+        }
       }
-      if (sub == 0) D.H[cell] = settle(hv);
+      seg_min<G>(hv);
+      if (ok && sub == 0) D.H[cell] = settle(hv);
     }
     // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side mismatch
     {
       int64_t iv = SD_INF;
       if (ok && g >= 7) {
         const int no = F.nout(a), ni = F.nin(b);
+#pragma unroll 1
         for (int q = sub; q < no * ni; q += G) {
           const int k2 = q % ni, k1 = q / ni;
           const SdEdge e1 = F.out(a, k1), e2 = F.in(b, k2);
@@ -773,21 +776,21 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       seg_min<G>(iv);
       if (ok && sub == 0) D.Ihat[rcell + s] = settle(iv);
     }
-    // typed closed values (every thread of the group) and Eq. (branch)
-    int64_t vv[6];
+    // typed closed values V_t, thread t of the group taking type t (G >= 8),
+    // then Eq. (branch) B and the bulge term WB (inner pair (a, b)) as group
+    // minima over the types
     {
-      const int oma = ok ? D.out_mask[a] : 0, nib = ok ? F.nin(b) : 0;
-      const int imb = ok ? D.in_mask[b] : 0;
-      int64_t B = SD_INF;
-#pragma unroll
-      for (int t = 0; t < 6; t++) {
-        int64_t v = SD_INF;
-        // the out-edge of a labelled with the pair's 5' nucleotide (a DFA has
-        // at most one; out-edges are stored by label)
-        const int l5 = c_pair5[t];
-        if (ok && g >= 5 && ((oma >> l5) & 1) && ((imb >> c_pair3[t]) & 1)) {
+      const int t = sub;
+      int64_t v = SD_INF;
+      if (ok && t < 6 && g >= 5) {
+        // the pair's 5' and 3' nucleotides; the out-edge of a labelled with the
+        // 5' one (a DFA has at most one; out-edges are stored by label)
+        const int l5 = (0x323210 >> (4 * t)) & 15, l3 = (0x230123 >> (4 * t)) & 15;
+        const int oma = D.out_mask[a];
+        if (((oma >> l5) & 1) && ((D.in_mask[b] >> l3) & 1)) {
           const SdEdge e1 = F.out(a, __popc(oma & ((1 << l5) - 1)));
-          const int l3 = c_pair3[t];
+          const int nib = F.nin(b);
+#pragma unroll 1
           for (int k2 = 0; k2 < nib; k2++) {
             const SdEdge e2 = F.in(b, k2);
             if (e2.label != l3) continue;
@@ -797,24 +800,27 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
             TERM(2);
           }
         }
-        v = settle(v);
-        vv[t] = v;
-        if (ok && sub == t % G) D.V[(int64_t)cell * 6 + t] = v;
-        if (fin(v)) {
-          upd(B, v + fx(T.mlintern + T.au[t]));
-          TERM(1);
-        }
       }
+      v = settle(v);
+      if (ok && t < 6) D.V[(int64_t)cell * 6 + t] = v;
+      int64_t B = SD_INF, wbv = SD_INF;
+      if (fin(v)) {
+        B = v + fx(T.mlintern + T.au[t]);
+        wbv = v + fx(T.au[rev_type(t)]);
+        TERM(1);
+      }
+      seg_min<G>(B);
+      seg_min<G>(wbv);
       B = settle(B);
-      if (ok && sub == 0) D.Bv[cell] = B;
+      if (ok && sub == 0) {
+        D.Bv[cell] = B;
+        D.WB[rcell + s] = settle(wbv);
+      }
       if (ok) Bs[s] = B;
     }
-    // inner terms of this cell for the loops that will enclose it: the bulge
-    // term WB (inner pair (a, b)) and the one-nucleotide-side factors X(a, b)
-    // (inner pair (a, d), d -> b) and Y(a, b) (inner pair (c, b), a -> c) of
-    // the 1 x n and n x 1 loops
+    // the one-nucleotide-side factors X(a, b) (inner pair (a, d), d -> b) and
+    // Y(a, b) (inner pair (c, b), a -> c) of the 1 x n and n x 1 loops
     if (ok) {
-      if (sub == 0) D.WB[rcell + s] = settle(g >= 5 ? best_au(vv, T.au) : SD_INF);
       const int im = D.in_mask[a], om = D.out_mask[b];
       const int nib = F.nin(b), noa = F.nout(a);
       const int sp = g & (SD_XSPAN - 1);
@@ -824,6 +830,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         if (q < 4) {  // X(a, b)[p = lab]: inner pair (a, d) of span g-1
           if (!((im >> lab) & 1)) continue;
           if (g >= 6)
+#pragma unroll 1
             for (int k = 0; k < nib; k++) {
               const SdEdge e = F.in(b, k);
               int64_t vi[6];
@@ -838,6 +845,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         } else {  // Y(a, b)[r = lab]: inner pair (c, b) of span g-1
           if (!((om >> lab) & 1)) continue;
           if (g >= 6)
+#pragma unroll 1
             for (int k = 0; k < noa; k++) {
               const SdEdge e = F.out(a, k);
               int64_t vi[6];
@@ -874,6 +882,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // 1 x n: u on layer lu, l2 = j + 2 - lu in [3, 29], inner span lu - 1 - i >= 5
         const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
         if (ulo <= uhi)
+#pragma unroll 1
           for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
             const int lu = F.layer(u), us = u - F.ls(lu), l2 = j + 2 - lu;
             const int64_t h = GS.hr[j - lu][us * SD_W + sb];
@@ -895,6 +904,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // n x 1: w on layer lw, l1 = lw - i + 2 in [3, 29], inner span j - lw - 1 >= 5
         const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
         if (wlo <= whi)
+#pragma unroll 1
           for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
             const int lw = F.layer(w), ws = w - F.ls(lw), l1 = lw - i + 2;
             const int64_t h = GS.hl[lw - i][ws * SD_W + sa];
@@ -920,6 +930,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
             const int noa = F.nout(a);
             const int ro0 = F.fo_off[F.ls(j - 2)], nro = F.fo_off[F.ls(j - 1)] - ro0;
             const int cs0 = F.ls(i + 1), ds0 = F.ls(j - 2), us0 = F.ls(j - 1);
+#pragma unroll 1
             for (int k = sub; k < noa * nro; k += G) {
               const int kp = k / nro, kr = k - kp * nro;
               const SdEdge p2 = F.out(a, kp);
@@ -939,6 +950,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
             const int nib = F.nin(b);
             const int po0 = F.fo_off[F.ls(i + 1)], npo = F.fo_off[F.ls(i + 2)] - po0;
             const int ws0 = F.ls(i + 1), cs0 = F.ls(i + 2), ds0 = F.ls(j - 1);
+#pragma unroll 1
             for (int k = sub; k < npo * nib; k += G) {
               const int kp = k / nib, kr = k - kp * nib;
               const SdFlatEdge p2 = F.fo[po0 + kp];
@@ -984,6 +996,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       int64_t *Kc = D.KR + ((int64_t)((g & 3) * (n + 1) + i) * SD_SLOTS + s) * SD_KM;
       const int64_t *Kin = D.KR + (int64_t)(((g - 2) & 3) * (n + 1) + i + 1) * SD_SLOTS * SD_KM;
       const int nox = F.nout(x), niy = F.nin(y);
+#pragma unroll 1
       for (int m = sub; m <= SD_MAXTWO - 4; m += G) {
         int64_t km = SD_INF;
         const int64_t asym = fx(min(T.maxninio, T.ninio * m));
@@ -1014,8 +1027,10 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         // both sides >= 1: K_{m-2} of the state pair (x', y') one nucleotide inside
         if (m >= 2 && g >= 9)
+#pragma unroll 1
           for (int a2 = 0; a2 < nox; a2++) {
             const SdEdge e1 = F.out(x, a2);
+#pragma unroll 1
             for (int b2 = 0; b2 < niy; b2++) {
               const SdEdge e2 = F.in(y, b2);
               const int64_t kv =
@@ -1047,8 +1062,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const int cell = ok ? F.cs(i, sa, j, sb) : 0;
     int64_t s2 = SD_INF;
     if (ok) {
-      if (g >= 2 && sub == 0)
-        for (int k = 0; k < F.nin(b); k++) {
+      if (g >= 2)
+#pragma unroll 1
+        for (int k = sub; k < F.nin(b); k += G) {
           const SdEdge e = F.in(b, k);
           const int64_t v = ro(D.S2 + F.cs(i, sa, j - 1, e.other - js));
           if (!fin(v)) continue;
@@ -1057,6 +1073,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         }
       const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
+#pragma unroll 1
       for (int k = sub; k < cnt; k += G) {
         const int c = D.cand_c[off + k];
         const int lc = __ldg(&D.layer[c]);
@@ -1069,26 +1086,26 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     }
     seg_min<G>(s2);
     s2 = settle(s2);
+    // P_S (Eq. partitionable with S): S2 or one unpaired edge at either end,
+    // the group's threads taking the out-edges of a, then the in-edges of b
+    int64_t ps = SD_INF;
+    if (ok && g >= 2) {
+      const int noa = F.nout(a), nt = noa + F.nin(b);
+#pragma unroll 1
+      for (int k = sub; k < nt; k += G) {
+        const bool left = k < noa;
+        const SdEdge e = left ? F.out(a, k) : F.in(b, k - noa);
+        const int64_t v = ro(D.S1 + (left ? F.cs(i + 1, e.other - i1s, j, sb)
+                                         : F.cs(i, sa, j - 1, e.other - js)));
+        if (!fin(v)) continue;
+        upd(ps, v + e.cost + mlb);
+        TERM(2);
+      }
+    }
+    seg_min<G>(ps);
     if (ok && sub == 0) {
       D.S2[cell] = s2;
-      // P_S (Eq. partitionable with S) and S1 = min(B, P_S)
-      int64_t ps = s2;
-      if (g >= 2) {
-        for (int k = 0; k < F.nout(a); k++) {
-          const SdEdge e = F.out(a, k);
-          const int64_t v = ro(D.S1 + F.cs(i + 1, e.other - i1s, j, sb));
-          if (!fin(v)) continue;
-          upd(ps, v + e.cost + mlb);
-          TERM(2);
-        }
-        for (int k = 0; k < F.nin(b); k++) {
-          const SdEdge e = F.in(b, k);
-          const int64_t v = ro(D.S1 + F.cs(i, sa, j - 1, e.other - js));
-          if (!fin(v)) continue;
-          upd(ps, v + e.cost + mlb);
-          TERM(2);
-        }
-      }
+      upd(ps, s2);
       ps = settle(ps);
       int64_t s1 = ps;
       if (fin(Bs[s])) upd(s1, Bs[s]);
