@@ -641,6 +641,8 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d, int wclass) {
   d.Xc = c.take<int64_t>((size_t)N * 4 * SD_XSPAN * wclass);
   d.Yr = c.take<int64_t>((size_t)N * 4 * SD_XSPAN * wclass);
   d.KR = c.take<int64_t>((size_t)SD_KRING * (n + 1) * wclass * wclass * SD_KM);
+  d.GL = c.take<int64_t>((size_t)(n + 1) * SD_GAPW * wclass * wclass);
+  d.GR = c.take<int64_t>((size_t)(n + 1) * SD_GAPW * wclass * wclass);
   d.cand_cnt = c.take<int32_t>(N);
   d.cand_off = c.take<int64_t>(N);
   d.cand_cap = L.caps.empty() ? nullptr : c.take<int32_t>(N);

@@ -27,6 +27,7 @@
 #define SD_MAXIN_WIDE 32 // in-edges per state of a product lattice
 #define SD_RING 32       // diagonals kept for the windowed two-loop tables
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
+#define SD_GAPW (SD_MAXTWO + 1)  // spans 0..SD_MAXTWO of the gap mirrors GL / GR
 #define SD_AN 12         // two-loop factor entries per cell slot (9 used, 96 bytes)
 #define SD_XSPAN 32      // spans kept per state in the 1 x n / n x 1 factor tables
 #define SD_KM 25         // internal-loop sizes kept per state pair for extension
@@ -163,6 +164,14 @@ struct SdDesign {
   // [4 + r] the n x 1 loops (r leaving b), [8] the 2 x 3 and 3 x 2 loops;
   // each without the outer pair's own mismatch and edge costs
   int64_t *Af;
+  // Gap values near the diagonal by layer, (n+1)*SD_GAPW*SLOTS each, so that
+  // the fill stages the gap vectors of both ends of a layer pair with
+  // contiguous loads: GL[(x*SD_GAPW + l)*SLOTS + c*W + s] = H(slot s of layer
+  // x -> slot c of layer x+l), GR[(y*SD_GAPW + l)*SLOTS + c*W + s] = H(slot c
+  // of layer y-l -> slot s of layer y); l = 0 holds the identity (0 on the
+  // diagonal), empty slots +inf.  Reset at the start of every run, entries of
+  // span l written by the fill of span l.
+  int64_t *GL, *GR;
   int32_t *cand_cnt;      // N   |C_b|
   const int64_t *cand_off;// N   first entry of C_b
   const int32_t *cand_cap;// N   entries reserved for C_b, or null when each list has its

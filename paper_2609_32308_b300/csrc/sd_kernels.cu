@@ -254,8 +254,7 @@ struct Fv {
 // group: hl[l][c*W + s] = H(slot s of layer i -> slot c of layer i+l),
 // hr[l][c*W + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW;
 // the two-loop options read them many times.
-constexpr int SD_GAPW = SD_MAXTWO + 1;
-struct GapStage {
+struct alignas(16) GapStage {
   int64_t hl[SD_GAPW][SD_SLOTS], hr[SD_GAPW][SD_SLOTS];
 };
 
@@ -708,16 +707,19 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   const int i1s = active ? F.ls(i + 1) : 0;
   GapStage &GS = s_gap[threadIdx.x / G];
   {
-    const int lmax = min(SD_GAPW - 1, g - 1);  // spans below g only (this span is not filled yet)
-    for (int q = sub; q < SD_GAPW * SD_SLOTS; q += G) {
-      const int l = q / SD_SLOTS, c = (q / SD_W) % SD_W, sn = q % SD_W;
-      int64_t vl = SD_INF, vr = SD_INF;
-      if (active && l <= lmax) {
-        if (sn < wa && c < F.w(i + l)) vl = l == 0 ? (c == sn ? 0 : SD_INF) : ro(F.H + F.cs(i, sn, i + l, c));
-        if (sn < wb && c < F.w(j - l)) vr = l == 0 ? (c == sn ? 0 : SD_INF) : ro(F.H + F.cs(j - l, c, j, sn));
-      }
-      GS.hl[l][c * SD_W + sn] = vl;
-      GS.hr[l][c * SD_W + sn] = vr;
+    // the gap mirrors of layer i (from the left) and layer j (from the right):
+    // spans below g only (this span is not filled yet)
+    const int lmax = min(SD_GAPW - 1, g - 1);
+    const longlong2 *gl = reinterpret_cast<const longlong2 *>(D.GL + (int64_t)i * SD_GAPW * SD_SLOTS);
+    const longlong2 *gr = reinterpret_cast<const longlong2 *>(D.GR + (int64_t)j * SD_GAPW * SD_SLOTS);
+    longlong2 *hl = reinterpret_cast<longlong2 *>(&GS.hl[0][0]);
+    longlong2 *hr = reinterpret_cast<longlong2 *>(&GS.hr[0][0]);
+    const longlong2 inf2 = make_longlong2(SD_INF, SD_INF);
+#pragma unroll 1
+    for (int q = sub; q < SD_GAPW * SD_SLOTS / 2; q += G) {
+      const bool in = active && (2 * q) / SD_SLOTS <= lmax;
+      hl[q] = in ? ro(gl + q) : inf2;
+      hr[q] = in ? ro(gr + q) : inf2;
     }
     __syncwarp();
   }
@@ -754,7 +756,14 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         }
       }
       seg_min<G>(hv);
-      if (ok && sub == 0) D.H[cell] = settle(hv);
+      if (ok && sub == 0) {
+        hv = settle(hv);
+        D.H[cell] = hv;
+        if (g < SD_GAPW) {
+          D.GL[((int64_t)i * SD_GAPW + g) * SD_SLOTS + sb * SD_W + sa] = hv;
+          D.GR[((int64_t)j * SD_GAPW + g) * SD_SLOTS + sa * SD_W + sb] = hv;
+        }
+      }
     }
     // Ihat: inner pair (c,d) one nucleotide inside (a,b) and its loop-side mismatch
     {
@@ -1933,11 +1942,22 @@ __global__ void __launch_bounds__(TB_THREADS) k_traceback(const SdDesign *__rest
   }
 }
 
-__global__ void k_clear_cand(const SdDesign *__restrict__ designs) {
+// Start of a run: empty candidate lists, overflow flag clear, gap mirrors
+// reset to the identity (span 0) and +inf.
+__global__ void k_clear(const SdDesign *__restrict__ designs) {
   const SdDesign &D = designs[blockIdx.y];
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < D.N; v += gridDim.x * blockDim.x)
-    D.cand_cnt[v] = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) D.tb[3] = 0;
+  const int stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int v = t0; v < D.N; v += stride) D.cand_cnt[v] = 0;
+  if (t0 == 0) D.tb[3] = 0;
+  const int64_t total = (int64_t)(D.n + 1) * SD_GAPW * SD_SLOTS;
+  for (int64_t e = t0; e < total; e += stride) {
+    const int q = (int)(e % SD_SLOTS), l = (int)((e / SD_SLOTS) % SD_GAPW);
+    const int x = (int)(e / ((int64_t)SD_SLOTS * SD_GAPW));
+    const int c = q / SD_W, sn = q % SD_W;
+    const int64_t v = l == 0 && c == sn && sn < D.lstart[x + 1] - D.lstart[x] ? 0 : SD_INF;
+    D.GL[e] = v;
+    D.GR[e] = v;
+  }
 }
 
 // Retained candidates of one design by (codon position of the right endpoint,
@@ -2052,7 +2072,7 @@ extern "C" int SD_KFN(sd_k_count_ops)(const SdDesign *d_designs, int count, cons
   cudaStream_t st = (cudaStream_t)stream;
   if (count <= 0) return 0;
   if (cudaMemsetAsync(d_ops, 0, sizeof(unsigned long long) * count, st) != cudaSuccess) return -1;
-  k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
+  k_clear<<<dim3(64, count), 256, 0, st>>>(d_designs);
   if (launch_fill<true>(group, d_designs, count, ns, d_cpre, d_params, st, d_ops)) return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
@@ -2076,7 +2096,7 @@ extern "C" int SD_KFN(sd_k_run)(const SdDesign *d_designs, int count, const int 
     if (launches) *launches = 0;
     return 0;
   }
-  k_clear_cand<<<dim3(8, count), 256, 0, st>>>(d_designs);
+  k_clear<<<dim3(64, count), 256, 0, st>>>(d_designs);
   if (events) record(events[0], st);
   if (launch_fill<false>(group, d_designs, count, ns, d_cpre, d_params, st, nullptr)) return -1;
   if (events) record(events[1], st);

@@ -227,6 +227,8 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.Xc = (int64_t *)take((size_t)N * 4 * SD_XSPAN * SD_W * 8);
   d.Yr = (int64_t *)take((size_t)N * 4 * SD_XSPAN * SD_W * 8);
   d.KR = (int64_t *)take((size_t)SD_KRING * (n + 1) * SD_SLOTS * SD_KM * 8);
+  d.GL = (int64_t *)take((size_t)(n + 1) * SD_GAPW * SD_SLOTS * 8);
+  d.GR = (int64_t *)take((size_t)(n + 1) * SD_GAPW * SD_SLOTS * 8);
   d.cand_cnt = (int32_t *)take(N * 4);
   d.cand_off = (int64_t *)take(N * 8);
   d.cand_c = (int32_t *)take((cap > 0 ? cap : 1) * 4);
