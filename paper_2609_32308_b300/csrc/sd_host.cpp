@@ -1507,7 +1507,10 @@ extern "C" int sd_plan_dump(const sd_plan *p, int item, int32_t *layer, int64_t 
       if (cnt[bb] > 0 && cudaMemcpy(cc.data(), d.cand_c + off[bb], (size_t)cnt[bb] * 4,
                                     cudaMemcpyDeviceToHost) != cudaSuccess)
         return SD_ECUDA;
-      for (int k = 0; k < cnt[bb]; k++) cand[(int64_t)cc[k] * N + bb] = 1;
+      for (int k = 0; k < cnt[bb]; k++) {
+        const int c = it.L.lstart[cc[k] >> SD_CAND_SHIFT] + (cc[k] & ((1 << SD_CAND_SHIFT) - 1));
+        cand[(int64_t)c * N + bb] = 1;
+      }
     }
   }
   return SD_OK;

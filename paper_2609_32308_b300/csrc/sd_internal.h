@@ -27,6 +27,7 @@
 #define SD_MAXIN_WIDE 32 // in-edges per state of a product lattice
 #define SD_RING 32       // diagonals kept for the windowed two-loop tables
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
+#define SD_CAND_SHIFT 3  // slot bits of a candidate entry (layers hold at most 8 states)
 #define SD_GAPW (SD_MAXTWO + 1)  // spans 0..SD_MAXTWO of the gap mirrors GL / GR
 #define SD_AN 12         // two-loop factor entries per cell slot (9 used, 96 bytes)
 #define SD_XSPAN 32      // spans kept per state in the 1 x n / n x 1 factor tables
@@ -177,7 +178,8 @@ struct SdDesign {
   const int32_t *cand_cap;// N   entries reserved for C_b, or null when each list has its
                           //     worst-case room; a list that outgrows a presized room sets
                           //     tb[3] (the run is then repeated with worst-case room)
-  int32_t *cand_c;        // start states of the retained candidates
+  int32_t *cand_c;        // start states of the retained candidates, by position:
+                          //   (layer << SD_CAND_SHIFT) | slot on the layer
   int64_t *cand_B;        // their scalar branch costs B(c,b)
   int64_t *Ext;           // N   exterior suffix values (Sec. 5 final-column exterior)
   char *mrna, *structure; // n+1 each

@@ -40,6 +40,8 @@
 #define SD_KFN(name) name##_wide
 #endif
 
+static_assert(SD_W <= (1 << SD_CAND_SHIFT), "a candidate entry holds the slot in SD_CAND_SHIFT bits");
+
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
@@ -1084,10 +1086,10 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       const int64_t off = D.cand_off[b];
 #pragma unroll 1
       for (int k = sub; k < cnt; k += G) {
-        const int c = D.cand_c[off + k];
-        const int lc = __ldg(&D.layer[c]);
+        const int ce = D.cand_c[off + k];
+        const int lc = ce >> SD_CAND_SHIFT;
         if (lc <= i) break;  // entries are in decreasing layer order
-        const int64_t v = ro(D.S1 + F.cs(i, sa, lc, c - F.ls(lc)));
+        const int64_t v = ro(D.S1 + F.cs(i, sa, lc, ce & ((1 << SD_CAND_SHIFT) - 1)));
         if (!fin(v)) continue;
         upd(s2, v + D.cand_B[off + k]);
         TERM(1);
@@ -1136,7 +1138,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         // finite direct interval (the sparse and dense S2 are equal, Thm. 1)
         if (D.dense ? fin(Bs[s]) : Bs[s] < PSs[s]) {
           if (cnt < cap) {
-            D.cand_c[off + cnt] = a0 + sa;
+            D.cand_c[off + cnt] = (i << SD_CAND_SHIFT) | sa;
             D.cand_B[off + cnt] = Bs[s];
           } else {
             D.tb[3] = 1;  // presized room exceeded: this run is repeated
@@ -1843,8 +1845,9 @@ __global__ void __launch_bounds__(TB_THREADS) k_traceback(const SdDesign *__rest
       const int cnt = D.cand_cap ? min(D.cand_cnt[yb], D.cand_cap[yb]) : D.cand_cnt[yb];
       const int64_t off = D.cand_off[yb];
       for (int k = threadIdx.x; k < cnt; k += TB_THREADS) {
-        const int c = D.cand_c[off + k];
-        if (G.layer(c) <= lx) continue;
+        const int ce = D.cand_c[off + k], lc = ce >> SD_CAND_SHIFT;
+        if (lc <= lx) continue;
+        const int c = G.lstart(lc) + (ce & ((1 << SD_CAND_SHIFT) - 1));
         const int64_t w = G.S1(x, c);
         if (fin(w) && w + D.cand_B[off + k] == v) best = (unsigned long long)c < best ? c : best;
       }
@@ -1972,7 +1975,7 @@ __global__ void k_retention(const SdDesign *__restrict__ designs, int item, int3
     const int cnt = D.cand_cap ? min(D.cand_cnt[b], D.cand_cap[b]) : D.cand_cnt[b];
     const int64_t off = D.cand_off[b];
     for (int q = 0; q < cnt; q++) {
-      const int span = lb - D.layer[D.cand_c[off + q]];
+      const int span = lb - (D.cand_c[off + q] >> SD_CAND_SHIFT);
       const int band = min(7, max(0, 31 - __clz(span) - 2));
       atomicAdd(&hist[k * 8 + band], 1);
     }
