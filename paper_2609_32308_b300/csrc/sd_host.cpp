@@ -614,6 +614,7 @@ size_t carve(char *base, const HostLattice &L, SdDesign &d, int wclass) {
   d.maxin = L.maxin;
   d.lstart = c.take<int32_t>(n + 2);
   d.layer = c.take<int32_t>(N);
+  d.pos = c.take<int32_t>(N);
   d.out = c.take<SdEdge>(N * SD_MAXOUT);
   d.out_cnt = c.take<uint8_t>(N);
   d.in = c.take<SdEdge>(N * L.maxin);

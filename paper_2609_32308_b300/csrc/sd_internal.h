@@ -123,6 +123,7 @@ struct SdDesign {
   int32_t dense;          // 1: retain every finite direct interval (scalar-dense control)
   const int32_t *lstart;  // n+2
   const int32_t *layer;   // N
+  int32_t *pos;           // N: (layer << SD_CAND_SHIFT) | slot on the layer (set by k_clear)
   const SdEdge *out;      // N * SD_MAXOUT, by label
   const uint8_t *out_cnt; // N
   const SdEdge *in;       // N * maxin, by (label, source)

@@ -895,7 +895,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         if (ulo <= uhi)
 #pragma unroll 1
           for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
-            const int lu = F.layer(u), us = u - F.ls(lu), l2 = j + 2 - lu;
+            const int pu = __ldg(&D.pos[u]);
+            const int lu = pu >> SD_CAND_SHIFT, us = pu & ((1 << SD_CAND_SHIFT) - 1), l2 = j + 2 - lu;
             const int64_t h = GS.hr[j - lu][us * SD_W + sb];
             if (!fin(h)) continue;
             const int64_t base =
@@ -917,7 +918,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         if (wlo <= whi)
 #pragma unroll 1
           for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
-            const int lw = F.layer(w), ws = w - F.ls(lw), l1 = lw - i + 2;
+            const int pw = __ldg(&D.pos[w]);
+            const int lw = pw >> SD_CAND_SHIFT, ws = pw & ((1 << SD_CAND_SHIFT) - 1), l1 = lw - i + 2;
             const int64_t h = GS.hl[lw - i][ws * SD_W + sa];
             if (!fin(h)) continue;
             const int64_t base =
@@ -1945,12 +1947,16 @@ __global__ void __launch_bounds__(TB_THREADS) k_traceback(const SdDesign *__rest
   }
 }
 
-// Start of a run: empty candidate lists, overflow flag clear, gap mirrors
-// reset to the identity (span 0) and +inf.
+// Start of a run: empty candidate lists, overflow flag clear, the position of
+// every state, gap mirrors reset to the identity (span 0) and +inf.
 __global__ void k_clear(const SdDesign *__restrict__ designs) {
   const SdDesign &D = designs[blockIdx.y];
   const int stride = gridDim.x * blockDim.x, t0 = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int v = t0; v < D.N; v += stride) D.cand_cnt[v] = 0;
+  for (int v = t0; v < D.N; v += stride) {
+    D.cand_cnt[v] = 0;
+    const int l = D.layer[v];
+    D.pos[v] = (l << SD_CAND_SHIFT) | (v - D.lstart[l]);
+  }
   if (t0 == 0) D.tb[3] = 0;
   const int64_t total = (int64_t)(D.n + 1) * SD_GAPW * SD_SLOTS;
   for (int64_t e = t0; e < total; e += stride) {

@@ -203,6 +203,7 @@ size_t carve_fixed(char *base, const FixedLattice &L, SdDesign &d, SdDesign **re
   d.status_slot = 0;
   d.lstart = (int32_t *)take((n + 2) * 4);
   d.layer = (int32_t *)take(N * 4);
+  d.pos = (int32_t *)take(N * 4);
   d.out = (SdEdge *)take(N * SD_MAXOUT * sizeof(SdEdge));
   d.out_cnt = (uint8_t *)take(N);
   d.in = (SdEdge *)take(N * SD_MAXIN * sizeof(SdEdge));
