@@ -891,7 +891,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       if (ok && g >= 7) {
         const int im = D.in_mask[a], om = D.out_mask[b];
         // 1 x n: u on layer lu, l2 = j + 2 - lu in [3, 29], inner span lu - 1 - i >= 5
-        const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
+        // (narrow layers: by row and column after this loop)
+        const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = SD_W == 2 ? -1 : j - 1;
         if (ulo <= uhi)
 #pragma unroll 1
           for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
@@ -914,7 +915,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
               }
           }
         // n x 1: w on layer lw, l1 = lw - i + 2 in [3, 29], inner span j - lw - 1 >= 5
-        const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
+        const int wlo = i + 1, whi = SD_W == 2 ? -1 : min(i + SD_MAXTWO - 3, j - 6);
         if (wlo <= whi)
 #pragma unroll 1
           for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
@@ -980,12 +981,102 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         }
       }
-      const int64_t af8 = seg_min8<G>(af, sub);
+      const int64_t af8 = SD_W == 2 ? SD_INF : seg_min8<G>(af, sub);
       seg_min<G>(af[8]);
       if (ok) {
         int64_t *Afc = D.Af + (int64_t)(rcell + s) * SD_AN;
-        if (sub < 8) Afc[sub] = settle(af8);
+        if (SD_W > 2 && sub < 8) Afc[sub] = settle(af8);
         if (sub == 0) Afc[8] = settle(af[8]);
+      }
+    }
+  }
+  // Narrow layers: the 1 x n factors Af[p] by row (the state a of slot sa and
+  // both slots of layer j at once: the window of u and the X values are the
+  // same for the row) and the n x 1 factors Af[4 + r] by column (the state b
+  // of slot sb and both slots of layer i: the window of w and the Y values are
+  // the same for the column).  acc[side * 4 + label] holds the two slots of
+  // the other end; the group minimum leaves value (sub & 7) in thread sub.
+  if constexpr (SD_W == 2) {
+    const int kr = (int)__reduce_max_sync(FULL, (unsigned)(active ? max(wa, wb) : 0));
+#pragma unroll 1
+    for (int k = 0; k < kr; k++) {
+      // row sa = k (1 x n)
+      {
+        const bool ok = active && k < wa;
+        int64_t acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[q] = SD_INF;
+        const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
+        if (ok && g >= 7 && ulo <= uhi) {
+          const int a = a0 + k, im = D.in_mask[a];
+#pragma unroll 1
+          for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
+            const int pu = __ldg(&D.pos[u]);
+            const int lu = pu >> SD_CAND_SHIFT, us = pu & ((1 << SD_CAND_SHIFT) - 1), l2 = j + 2 - lu;
+            const int64_t h0 = GS.hr[j - lu][us * SD_W], h1 = GS.hr[j - lu][us * SD_W + 1];
+            if (!fin(h0) && !fin(h1)) continue;
+            const int64_t e = fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
+            const int64_t *xc =
+                D.Xc + ((int64_t)a * 4 * SD_XSPAN + ((lu - i) & (SD_XSPAN - 1))) * SD_W + us;
+#pragma unroll
+            for (int p = 0; p < 4; p++)
+              if ((im >> p) & 1) {
+                const int64_t x = ro(xc + p * SD_XSPAN * SD_W);
+                if (!fin(x)) continue;
+                if (fin(h0)) {
+                  upd(acc[p], x + h0 + e);
+                  TERM(2);
+                }
+                if (fin(h1)) {
+                  upd(acc[4 + p], x + h1 + e);
+                  TERM(2);
+                }
+              }
+          }
+        }
+        const int64_t v = seg_min8<G>(acc, sub);
+        const int sb = (sub >> 2) & 1;
+        if (ok && sub < 8 && sb < wb)
+          D.Af[(int64_t)(rcell + k * SD_W + sb) * SD_AN + (sub & 3)] = settle(v);
+      }
+      // column sb = k (n x 1)
+      {
+        const bool ok = active && k < wb;
+        int64_t acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) acc[q] = SD_INF;
+        const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
+        if (ok && g >= 7 && wlo <= whi) {
+          const int b = b0 + k, om = D.out_mask[b];
+#pragma unroll 1
+          for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
+            const int pw = __ldg(&D.pos[w]);
+            const int lw = pw >> SD_CAND_SHIFT, ws = pw & ((1 << SD_CAND_SHIFT) - 1), l1 = lw - i + 2;
+            const int64_t h0 = GS.hl[lw - i][ws * SD_W], h1 = GS.hl[lw - i][ws * SD_W + 1];
+            if (!fin(h0) && !fin(h1)) continue;
+            const int64_t e = fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
+            const int64_t *yr =
+                D.Yr + ((int64_t)b * 4 * SD_XSPAN + ((j - lw) & (SD_XSPAN - 1))) * SD_W + ws;
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+              if ((om >> r) & 1) {
+                const int64_t y = ro(yr + r * SD_XSPAN * SD_W);
+                if (!fin(y)) continue;
+                if (fin(h0)) {
+                  upd(acc[r], y + h0 + e);
+                  TERM(2);
+                }
+                if (fin(h1)) {
+                  upd(acc[4 + r], y + h1 + e);
+                  TERM(2);
+                }
+              }
+          }
+        }
+        const int64_t v = seg_min8<G>(acc, sub);
+        const int sa = (sub >> 2) & 1;
+        if (ok && sub < 8 && sa < wa)
+          D.Af[(int64_t)(rcell + sa * SD_W + k) * SD_AN + 4 + (sub & 3)] = settle(v);
       }
     }
   }
