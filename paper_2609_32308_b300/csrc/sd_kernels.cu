@@ -260,33 +260,6 @@ struct alignas(16) GapStage {
   int64_t hl[SD_GAPW][SD_SLOTS], hr[SD_GAPW][SD_SLOTS];
 };
 
-// The states of the layers lo..hi as entries k = 0 .. cnt-1, each a (layer,
-// slot) pair.  With narrow layers every (layer, slot) pair is an entry and
-// the caller's staged gap value, +inf past the width of its layer, rejects
-// the empty slots: no lattice lookup per entry.  Wide layers walk the states.
-struct LayerRange {
-  int lo, base, cnt;
-  __device__ __forceinline__ LayerRange(const Fv &F, int lo_, int hi) : lo(lo_), base(0), cnt(0) {
-    if (hi < lo) return;
-    if (SD_W == 2) {
-      cnt = (hi - lo + 1) * SD_W;
-    } else {
-      base = F.ls(lo);
-      cnt = F.ls(hi + 1) - base;
-    }
-  }
-  __device__ __forceinline__ void at(const Fv &F, int k, int &l, int &s) const {
-    if (SD_W == 2) {
-      l = lo + k / SD_W;
-      s = k % SD_W;
-    } else {
-      const int v = base + k;
-      l = F.layer(v);
-      s = v - F.ls(l);
-    }
-  }
-};
-
 // the type of the same pair read from the other strand (AU <-> UA, CG <-> GC,
 // GU <-> UG)
 __device__ __forceinline__ int rev_type(int t) { return t < 4 ? 3 - t : 9 - t; }
@@ -402,16 +375,16 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
   if (g < 5) return;
   // ---- stack and bulges: right side (l1 = 0, l2 = l >= 0), left side (l2 = 0, l1 = l >= 1) ----
   {
-    // layers of d on the right side, of c on the left side
-    const LayerRange R(F, max(ly - SD_MAXTWO, lx + 5), ly), Lf(F, lx + 1, min(lx + SD_MAXTWO, ly - 5));
-    const int nr = R.cnt;
+    // the states d of the right side, c of the left side
+    const int r0 = F.ls(max(ly - SD_MAXTWO, lx + 5)), nr = F.ls(ly + 1) - r0;
+    const int lhi = min(lx + SD_MAXTWO, ly - 5);
+    const int nl = lhi >= lx + 1 ? F.ls(lhi + 1) - lx1s : 0;
     int64_t bul = SD_INF;  // bulges l >= 2: inner part, AU(t) added once below
 #pragma unroll 1
-    for (int k = sub; k < nr + Lf.cnt; k += G) {
+    for (int k = sub; k < nr + nl; k += G) {
       const bool right = k < nr;
-      int lv, sv;
-      if (right) R.at(F, k, lv, sv);
-      else Lf.at(F, k - nr, lv, sv);
+      const int pv = __ldg(&D.pos[right ? r0 + k : lx1s + k - nr]);
+      const int lv = pv >> SD_CAND_SHIFT, sv = pv & ((1 << SD_CAND_SHIFT) - 1);
       const int l = right ? ly - lv : lv - lx;
       // staged gap (l = 0: 0 on y itself, +inf elsewhere)
       const int64_t h = right ? GS.hr[l][sv * SD_W + sy] : GS.hl[l][sv * SD_W + sx];
