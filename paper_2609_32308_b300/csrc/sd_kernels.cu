@@ -211,13 +211,11 @@ struct Fv {
   const uint8_t *__restrict__ in_;
   const int64_t *H;
   const int64_t *V;
-  const int32_t *__restrict__ lay;
   const SdFlatEdge *__restrict__ fo;
   const int32_t *__restrict__ fo_off;
   const SdFlatEdge *__restrict__ fi;
   const int32_t *__restrict__ fi_off;
   __device__ __forceinline__ int ls(int l) const { return __ldg(lst + l); }
-  __device__ __forceinline__ int layer(int v) const { return __ldg(lay + v); }
   __device__ __forceinline__ int w(int l) const { return __ldg(lst + l + 1) - __ldg(lst + l); }
   __device__ __forceinline__ int doff(int s) const { return (s - 1) * (n + 1) - (((s - 1) * s) >> 1); }
   // full-table entry of (layer lx, slot sx) -> (layer ly, slot sy), ly > lx
@@ -664,7 +662,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   F.in_ = D.in_cnt;
   F.H = D.H;
   F.V = D.V;
-  F.lay = D.layer;
   F.fo = D.fo;
   F.fo_off = D.fo_off;
   F.fi = D.fi;
@@ -1310,7 +1307,6 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       Fo.in_ = Do.in_cnt;
       Fo.H = Do.H;
       Fo.V = Do.V;
-      Fo.lay = Do.layer;
       Fo.fo = Do.fo;
       Fo.fo_off = Do.fo_off;
       Fo.fi = Do.fi;
