@@ -1241,7 +1241,7 @@ int regrow_if_needed(sd_plan *p) {
     if (it.status != SD_OK || !it.d.cand_cap) continue;
     int64_t flag = 0;
     if (cudaMemcpy(&flag, it.d.tb + 3, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return SD_ECUDA;
-    if (flag) by_dev.push_back({it.dev_index, (int)k});
+    if (flag & SD_TB_OVERFLOW) by_dev.push_back({it.dev_index, (int)k});
   }
   if (by_dev.empty()) return SD_OK;
   std::sort(by_dev.begin(), by_dev.end());
@@ -1345,7 +1345,8 @@ extern "C" int sd_plan_results(sd_plan *p, sd_result *outs, int *status) {
         r.n = n;
         r.energy = (int32_t)tb[0];
         r.objective_fx = ext0;
-        if (ext0 >= SD_FINLIM) st = SD_EINFEASIBLE;
+        if (tb[3] & SD_TB_WAIT) st = SD_EINTERNAL;  // a fill wait gave up
+        else if (ext0 >= SD_FINLIM) st = SD_EINFEASIBLE;
         else if (tb[2] != 0 || tb[0] * 4294967296LL + tb[1] != ext0) st = SD_EINTERNAL;
         // FP64 objective from the emitted codons, in codon order
         double cc = 0.0;

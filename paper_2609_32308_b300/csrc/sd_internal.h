@@ -41,6 +41,9 @@
 // finite iff it is < 2^59, and never overflows.
 #define SD_INF (1LL << 60)
 #define SD_FINLIM (1LL << 59)
+// flags in tb[3] of a design (set by the fill, cleared at the start of a run)
+#define SD_TB_OVERFLOW 1  // a presized candidate list overflowed: the run is repeated
+#define SD_TB_WAIT 2      // a bounded wait of the fill gave up: the run is invalid
 #define SD_EXT_INF (1LL << 62)   // +inf in the dense dump layout
 
 struct SdEdge {

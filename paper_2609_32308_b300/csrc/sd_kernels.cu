@@ -605,6 +605,59 @@ struct FillShape {
 };
 
 
+// Bulk copy of one row of a gap mirror into shared memory (16-byte aligned
+// addresses, a multiple of 16 bytes), completing on the group's barrier.
+constexpr uint32_t SD_GAP_ROW = SD_GAPW * SD_SLOTS * 8;
+static_assert(SD_GAP_ROW % 16 == 0, "bulk copies move multiples of 16 bytes");
+__device__ __forceinline__ void bulk_row(uint32_t dst, const int64_t *src, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(SD_GAP_ROW), "r"(bar)
+      : "memory");
+}
+// Wait for phase 0 of a transaction barrier for at most ~1 s of SM clock.
+__device__ __forceinline__ bool wait_phase0(uint32_t bar) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n"
+        " selp.u32 %0, 1, 0, p;\n}" : "=r"(done) : "r"(bar) : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+// Stage the group's two gap rows; false when some group's copies in the warp
+// did not complete in time (every design of the warp's layer pairs is flagged
+// invalid and the warp leaves).
+__device__ __forceinline__ bool stage_gap_rows(const SdDesign &D, bool active, int sub, int i,
+                                               int j, GapStage &GS, uint64_t &barw) {
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&barw);
+  if (active && sub == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(2 * SD_GAP_ROW)
+                 : "memory");
+    bulk_row((uint32_t)__cvta_generic_to_shared(&GS.hl[0][0]),
+             D.GL + (int64_t)i * SD_GAPW * SD_SLOTS, bar);
+    bulk_row((uint32_t)__cvta_generic_to_shared(&GS.hr[0][0]),
+             D.GR + (int64_t)j * SD_GAPW * SD_SLOTS, bar);
+  }
+  __syncwarp();
+  const bool late = active && !wait_phase0(bar);
+  if (__any_sync(FULL, late)) {
+    if (active && sub == 0) {
+      // this layer pair stays unfilled
+      atomicOr(reinterpret_cast<unsigned long long *>(&D.tb[3]), (unsigned long long)SD_TB_WAIT);
+      if (late) wait_phase0(bar);  // the copies may still be in flight into this block's memory
+    }
+    __syncwarp();
+    return false;
+  }
+  return true;
+}
+
 #ifndef SD_FILL_MINB
 #define SD_FILL_MINB 5
 #endif
@@ -616,6 +669,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   constexpr int NT = FillShape<G>::threads;
   __shared__ SmallTables T;
   __shared__ GapStage s_gap[FillShape<G>::pairs];
+  __shared__ uint64_t s_bar[FillShape<G>::pairs];  // one transaction barrier per group
   {
     const int32_t *src[] = {&Pp->stack[0][0], &Pp->mmH[0][0], &Pp->bulge[0], &Pp->au[0],
                             &Pp->ninio};
@@ -678,23 +732,12 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   const int js = active ? F.ls(j - 1) : 0;  // first state on layer j-1
   const int i1s = active ? F.ls(i + 1) : 0;
   GapStage &GS = s_gap[threadIdx.x / G];
-  {
-    // the gap mirrors of layer i (from the left) and layer j (from the right):
-    // spans below g only (this span is not filled yet)
-    const int lmax = min(SD_GAPW - 1, g - 1);
-    const longlong2 *gl = reinterpret_cast<const longlong2 *>(D.GL + (int64_t)i * SD_GAPW * SD_SLOTS);
-    const longlong2 *gr = reinterpret_cast<const longlong2 *>(D.GR + (int64_t)j * SD_GAPW * SD_SLOTS);
-    longlong2 *hl = reinterpret_cast<longlong2 *>(&GS.hl[0][0]);
-    longlong2 *hr = reinterpret_cast<longlong2 *>(&GS.hr[0][0]);
-    const longlong2 inf2 = make_longlong2(SD_INF, SD_INF);
-#pragma unroll 1
-    for (int q = sub; q < SD_GAPW * SD_SLOTS / 2; q += G) {
-      const bool in = active && (2 * q) / SD_SLOTS <= lmax;
-      hl[q] = in ? ro(gl + q) : inf2;
-      hr[q] = in ? ro(gr + q) : inf2;
-    }
-    __syncwarp();
-  }
+  // The gap mirrors of layer i (from the left) and layer j (from the right),
+  // one contiguous row each, copied into the group's stage by two bulk
+  // asynchronous copies that one thread issues and a transaction barrier
+  // tracks.  Entries of spans >= g still hold the +inf of the run's reset (the
+  // mirrors of span l are written by the launch of span l).
+  if (!stage_gap_rows(D, active, sub, i, j, GS, s_bar[threadIdx.x / G])) return;
 
   int64_t Bs[SD_SLOTS], PSs[SD_SLOTS];
 #pragma unroll
@@ -1204,7 +1247,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
             D.cand_c[off + cnt] = (i << SD_CAND_SHIFT) | sa;
             D.cand_B[off + cnt] = Bs[s];
           } else {
-            D.tb[3] = 1;  // presized room exceeded: this run is repeated
+            // presized room exceeded: this run is repeated
+            atomicOr(reinterpret_cast<unsigned long long *>(&D.tb[3]), (unsigned long long)SD_TB_OVERFLOW);
           }
           cnt++;
         }
