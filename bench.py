@@ -247,8 +247,9 @@ def cpu_baseline():
 
 def run_reference(args):
     """The oracle timed as the reference arm (rank 0 only): each step times a
-    bounded sample (one 60-aa and one 120-aa protein on all host cores) and
-    extrapolates its 925-aa design time with the sample's growth rate."""
+    bounded sample (one protein of --cpu-sample-aa / 2 and one of --cpu-sample-aa
+    amino acids, 40 and 80 by default, on all host cores) and extrapolates its
+    925-aa design time with the sample's growth rate."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
