@@ -355,12 +355,12 @@ def extras(sd, E, stream, pred, args):
                              "Z": r["Z"], "Z_over_n2": r["Z"] / n ** 2,
                              "status": r["status"]}
     plan.free()
-    # batch-size sweep at 925 aa, lambda = 4 (fill group 8, presized, graph)
+    # batch-size sweep at 925 aa, lambda = 4 (fill group by span, presized, graph)
     sweep = {}
     for B in [int(x) for x in args.sweep.split(",") if x]:
         prots, ws, lams = workload(B, 0)
         plan = sd.Plan(E, prots, ws, lams, predictor=pred, margin=2.0)
-        plan.group = 8
+        plan.group = sd.SD_GROUP_BY_SPAN
         plan.set_graph(True)
         plan.run(stream)
         res = plan.results()
@@ -426,7 +426,7 @@ def extras(sd, E, stream, pred, args):
         t_build = time.perf_counter()
         plan = sd.Plan(E, prots, ws, lams, predictor=pred, margin=2.0)
         t_build = time.perf_counter() - t_build
-        plan.group = 8
+        plan.group = sd.SD_GROUP_BY_SPAN
         mixed = {"proteins": len(prots), "aa_total": sum(lengths), "max_aa": max(lengths),
                  "device_gb": plan.device_bytes / 1e9, "plan_create_s": t_build}
         ref = None
@@ -477,17 +477,18 @@ def main():
     peaks = measured_alu_peaks()              # before any timed work
 
     # ---------------- batched: inputs resident in HBM ----------------
-    # launch order: W warm-up steps (the first three are the autotuner's runs,
-    # one per group size), then K timed steps, each one graph replay
+    # launch order: the autotuner's four runs (one per group choice: by span,
+    # 8, 16, 32) as warm-up steps, W - 4 more if W > 4, the graph capture,
+    # then K timed steps, each one graph replay
     pred = None
     if not args.no_predictor:
         from paper_2609_32308_b300 import retention
         pred = retention.load()
     plan = sd.Plan(E, prots, ws, lams, predictor=pred, margin=2.0)
-    tune = plan.autotune()                     # 3 warm-up steps
+    tune = plan.autotune()                     # 4 warm-up steps
     plan.set_graph(True)
     plan.set_timing(True)
-    for _ in range(max(0, args.warmup - 3)):
+    for _ in range(max(0, args.warmup - 4)):
         plan.run(stream)
     # a presized list that overflowed is regrown here, before the timed steps
     warm = plan.results()

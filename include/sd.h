@@ -110,8 +110,9 @@ void sd_energy_free(sd_energy *e);
  *   lambda        >= 0, kcal/mol.
  * Fills *out (caller-owned struct; buffers freed by sd_result_free).
  * Returns SD_OK or SD_EINVAL / SD_ERANGE / SD_ENOMEM / SD_ECUDA / SD_EINTERNAL,
- * or SD_EINFEASIBLE when the design language is empty (no complete mRNA; a
- * protein alone always has one, forbidden motifs can remove them all). */
+ * SD_EINFEASIBLE when the design language is empty (no complete mRNA; a
+ * protein alone always has one, forbidden motifs can remove them all), or
+ * SD_ETIMEOUT when a bounded wait inside the fill expired (no design). */
 int sd_design(const sd_energy *energy, const char *protein, const double *codon_weights,
               double lambda, sd_result *out);
 
@@ -204,8 +205,8 @@ int sd_inverse_lambda(const sd_energy *energy, const char *protein, const double
  * All calls share the scratch: calls that overlap on the GPU (two host
  * threads, or work still in flight) race and must be serialised.
  * Runs on the legacy default stream and returns when the design is complete.
- * Returns SD_OK, SD_EINVAL, SD_ERANGE, SD_ESIZE, SD_ECUDA, SD_EINTERNAL or
- * SD_EINFEASIBLE (empty design language, as for sd_design). */
+ * Returns SD_OK, SD_EINVAL, SD_ERANGE, SD_ESIZE, SD_ECUDA, SD_EINTERNAL,
+ * SD_EINFEASIBLE (empty design language, as for sd_design) or SD_ETIMEOUT. */
 int sd_design_noalloc(const sd_energy *energy, const char *protein, const double *codon_weights,
                       double lambda, sd_result *out);
 
@@ -253,15 +254,21 @@ int sd_plan_phase_times(const sd_plan *plan, float *ms3);
  * does, but without the exterior pass and the traceback. */
 int sd_plan_count_ops(sd_plan *plan, int64_t *ops);
 
-/* Threads cooperating on one layer pair in the fill: 8, 16 or 32; anything
- * else is SD_EINVAL.  The default is 8 when the designs of the plan have at
- * least 16,384 nucleotides in total (many layer pairs per span), else 32.  Results do not depend on it; speed does.
+/* Threads cooperating on one layer pair in the fill: 8, 16 or 32, or
+ * SD_GROUP_BY_SPAN (0): per span, 8 while the span's layer pairs fill the
+ * GPU with resident blocks of the group-8 fill, then 16 while they fill it at
+ * group 16, then 32 (the late spans, too small for one wave, give every layer
+ * pair more threads).  Anything else is SD_EINVAL.  The default is
+ * SD_GROUP_BY_SPAN.  Plans of wide layers (motif products) always run groups
+ * of 32.  Results do not depend on the group; speed does.
  * sd_plan_autotune runs the plan once per candidate (synchronously, legacy
- * default stream), keeps the fastest and writes the three fill times (ms, in
- * the order 8, 16, 32) to ms3 (may be NULL). */
+ * default stream), keeps the fastest and writes the four fill times (ms, in
+ * the order SD_GROUP_BY_SPAN, 8, 16, 32; only the first for wide layers) to
+ * ms4 (may be NULL). */
+#define SD_GROUP_BY_SPAN 0
 int sd_plan_set_group(sd_plan *plan, int group);
 int sd_plan_get_group(const sd_plan *plan);
-int sd_plan_autotune(sd_plan *plan, float *ms3);
+int sd_plan_autotune(sd_plan *plan, float *ms4);
 
 /* Capture the whole run (fill, exterior pass, traceback: one launch per span)
  * into a CUDA graph on the next sd_plan_run and replay the graph on later runs

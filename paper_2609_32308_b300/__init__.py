@@ -23,6 +23,7 @@ _lib = None
 SD_OK, SD_EINVAL, SD_ERANGE, SD_EINFEASIBLE = 0, -1, -2, -3
 SD_ENOMEM, SD_ECUDA, SD_ETIMEOUT, SD_EINTERNAL, SD_ESIZE = -4, -5, -6, -7, -8
 SD_LAYOUT_SPAN, SD_LAYOUT_SQUARE, SD_LAYOUT_PACKED = 0, 1, 2
+SD_GROUP_BY_SPAN = 0  # fill group chosen per span (sd_plan_set_group)
 INF = 1 << 62          # +infinity in table dumps
 FX_ONE = 1 << 32       # one dcal/mol in the fixed-point unit
 
@@ -396,11 +397,11 @@ class Plan:
 
     def autotune(self):
         """Pick the fastest group size; returns {group: fill ms}."""
-        ms = np.zeros(3, dtype=np.float32)
+        ms = np.zeros(4, dtype=np.float32)
         rc = lib().sd_plan_autotune(self.handle, _ptr(ms))
         if rc != SD_OK:
             raise SdError(rc, "sd_plan_autotune")
-        return dict(zip((8, 16, 32), (float(x) for x in ms)))
+        return dict(zip((SD_GROUP_BY_SPAN, 8, 16, 32), (float(x) for x in ms)))
 
     def count_ops(self):
         """Algorithmic INT32 slots of the fill, per item (counting variant)."""

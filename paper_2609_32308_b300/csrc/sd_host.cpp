@@ -912,7 +912,7 @@ int plan_create(const sd_energy *energy, const sd_predictor *cpred, double margi
     p->cpre_host = cpre;
     // default fill group: 8 threads per layer pair when a span holds many
     // layer pairs (a large batch), else 32 (sd_plan_autotune measures)
-    p->group = p->wclass != SD_W ? 32 : cpre.back() >= 16384 ? 8 : 32;
+    p->group = p->wclass != SD_W ? 32 : SD_GROUP_BY_SPAN;
   }
   if (!p->hdesigns.empty()) {
     if (cudaMalloc(&p->arena, total) != cudaSuccess) {
@@ -1163,7 +1163,8 @@ extern "C" int sd_plan_set_timing(sd_plan *p, int enable);
 extern "C" int sd_plan_phase_times(const sd_plan *p, float *ms);
 
 extern "C" int sd_plan_set_group(sd_plan *p, int group) {
-  if (!p || !(group == 8 || group == 16 || group == 32)) return SD_EINVAL;
+  if (!p || !(group == SD_GROUP_BY_SPAN || group == 8 || group == 16 || group == 32))
+    return SD_EINVAL;
   if (group != p->group && p->gexec) {
     cudaGraphExecDestroy(p->gexec);
     p->gexec = nullptr;
@@ -1178,15 +1179,16 @@ extern "C" int sd_plan_get_group(const sd_plan *p) { return p ? p->group : SD_EI
 // events on the legacy default stream) and keep the fastest.
 extern "C" int sd_plan_autotune(sd_plan *p, float *ms_out) {
   if (!p) return SD_EINVAL;
-  static const int cand[3] = {8, 16, 32};
+  static const int cand[4] = {SD_GROUP_BY_SPAN, 8, 16, 32};
   if (p->hdesigns.empty()) return SD_OK;
   const bool had = p->timing;
   int rc = sd_plan_set_timing(p, 1);
   if (rc != SD_OK) return rc;
   float best = 0.0f;
   int best_g = p->group;
-  for (int k = 0; k < 3; k++) {
-    p->group = cand[k];
+  const int ncand = p->wclass != SD_W ? 1 : 4;  // wide layers: groups of 32 only
+  for (int k = 0; k < ncand; k++) {
+    p->group = p->wclass != SD_W ? 32 : cand[k];
     rc = sd_plan_run(p, nullptr);
     if (rc != SD_OK) break;
     float ms[3];
@@ -1195,7 +1197,7 @@ extern "C" int sd_plan_autotune(sd_plan *p, float *ms_out) {
     if (ms_out) ms_out[k] = ms[0];
     if (k == 0 || ms[0] < best) {
       best = ms[0];
-      best_g = cand[k];
+      best_g = p->group;
     }
   }
   p->group = best_g;
@@ -1345,7 +1347,7 @@ extern "C" int sd_plan_results(sd_plan *p, sd_result *outs, int *status) {
         r.n = n;
         r.energy = (int32_t)tb[0];
         r.objective_fx = ext0;
-        if (tb[3] & SD_TB_WAIT) st = SD_EINTERNAL;  // a fill wait gave up
+        if (tb[3] & SD_TB_WAIT) st = SD_ETIMEOUT;  // a fill wait gave up
         else if (ext0 >= SD_FINLIM) st = SD_EINFEASIBLE;
         else if (tb[2] != 0 || tb[0] * 4294967296LL + tb[1] != ext0) st = SD_EINTERNAL;
         // FP64 objective from the emitted codons, in codon order

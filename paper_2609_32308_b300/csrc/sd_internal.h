@@ -27,6 +27,9 @@
 #define SD_MAXIN_WIDE 32 // in-edges per state of a product lattice
 #define SD_RING 32       // diagonals kept for the windowed two-loop tables
 #define SD_MAXTWO 30     // max unpaired nucleotides in a bulge / internal loop
+#ifndef SD_GROUP_BY_SPAN
+#define SD_GROUP_BY_SPAN 0  // fill group chosen per span by its layer pairs (as in sd.h)
+#endif
 #define SD_CAND_SHIFT 3  // slot bits of a candidate entry (layers hold at most 8 states)
 #define SD_GAPW (SD_MAXTWO + 1)  // spans 0..SD_MAXTWO of the gap mirrors GL / GR
 #define SD_AN 12         // two-loop factor entries per cell slot (9 used, 96 bytes)

@@ -2121,9 +2121,18 @@ __global__ void k_count(const SdDesign *__restrict__ designs, unsigned long long
 // One launch per span over the span's work queue.  ns: lengths of the
 // designs in device order (non-increasing); cpre: their prefix sums of n+1.
 template <int G, bool COUNT>
-void launch_fill_g(const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
-                   const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
+void launch_span(int g, int nact, int64_t items, const SdDesign *d_designs, const int32_t *d_cpre,
+                 const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
   constexpr int per_block = FillShape<G>::pairs;
+  dim3 grid((unsigned)((items + per_block - 1) / per_block));
+  k_fill_span<G, COUNT><<<grid, FillShape<G>::threads, 0, st>>>(d_designs, d_params, g, nact,
+                                                                (int)items, d_cpre, d_ops);
+}
+
+// Spans g = 1 .. the longest design (designs sorted by length, longest
+// first); a design shorter than g drops out.  f(g, nact, items) launches one.
+template <class Fn>
+void for_each_span(int count, const int *ns, Fn f) {
   int nact = count;
   int64_t cp = 0;
   for (int d = 0; d < count; d++) cp += ns[d] + 1;
@@ -2135,24 +2144,57 @@ void launch_fill_g(const SdDesign *d_designs, int count, const int *ns, const in
     }
     const int64_t items = cp - (int64_t)nact * g;
     if (items <= 0) break;
-    dim3 grid((unsigned)((items + per_block - 1) / per_block));
-    k_fill_span<G, COUNT><<<grid, FillShape<G>::threads, 0, st>>>(d_designs, d_params, g, nact,
-                                                                  (int)items, d_cpre, d_ops);
+    f(g, nact, items);
   }
+}
+
+// Group SD_GROUP_BY_SPAN: 8 threads per layer pair while a span fills the GPU
+// with resident group-8 blocks, then 16 while it fills it with group-16
+// blocks, then 32: the late spans, too small for one wave, give each layer
+// pair more threads (shorter dependent-load chains).
+template <bool COUNT>
+int span_waves(int64_t &wave8, int64_t &wave16) {
+  int dev = 0, sms = 0, b8 = 0, b16 = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b8, k_fill_span<8, COUNT>,
+                                                    FillShape<8>::threads, 0) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b16, k_fill_span<16, COUNT>,
+                                                    FillShape<16>::threads, 0) != cudaSuccess)
+    return -1;
+  wave8 = (int64_t)sms * b8 * FillShape<8>::pairs;
+  wave16 = (int64_t)sms * b16 * FillShape<16>::pairs;
+  return 0;
 }
 
 template <bool COUNT>
 int launch_fill(int G, const SdDesign *d_designs, int count, const int *ns, const int32_t *d_cpre,
                 const SdParams *d_params, cudaStream_t st, unsigned long long *d_ops) {
   if (SD_W > 2) G = 32;  // the wide instance has one group size
-  switch (G) {
 #if SD_W == 2
-    case 8: launch_fill_g<8, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
-    case 16: launch_fill_g<16, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
-#endif
-    case 32: launch_fill_g<32, COUNT>(d_designs, count, ns, d_cpre, d_params, st, d_ops); break;
-    default: return -1;
+  if (G == SD_GROUP_BY_SPAN) {
+    int64_t wave8 = 0, wave16 = 0;
+    if (span_waves<COUNT>(wave8, wave16)) return -1;
+    for_each_span(count, ns, [&](int g, int nact, int64_t items) {
+      if (items >= wave8)
+        launch_span<8, COUNT>(g, nact, items, d_designs, d_cpre, d_params, st, d_ops);
+      else if (items >= wave16)
+        launch_span<16, COUNT>(g, nact, items, d_designs, d_cpre, d_params, st, d_ops);
+      else
+        launch_span<32, COUNT>(g, nact, items, d_designs, d_cpre, d_params, st, d_ops);
+    });
+    return 0;
   }
+#endif
+  if (!(G == 32 || (SD_W == 2 && (G == 8 || G == 16)))) return -1;
+  for_each_span(count, ns, [&](int g, int nact, int64_t items) {
+#if SD_W == 2
+    if (G == 8) launch_span<8, COUNT>(g, nact, items, d_designs, d_cpre, d_params, st, d_ops);
+    else if (G == 16) launch_span<16, COUNT>(g, nact, items, d_designs, d_cpre, d_params, st, d_ops);
+    else
+#endif
+      launch_span<32, COUNT>(g, nact, items, d_designs, d_cpre, d_params, st, d_ops);
+  });
   return 0;
 }
 

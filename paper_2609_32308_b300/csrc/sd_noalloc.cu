@@ -308,7 +308,7 @@ extern "C" int sd_design_noalloc(const sd_energy *energy, const char *protein,
     return SD_ECUDA;
   mrna[n] = 0;
   structure[n] = 0;
-  if (tb[3] & SD_TB_WAIT) return SD_EINTERNAL;  // a fill wait gave up
+  if (tb[3] & SD_TB_WAIT) return SD_ETIMEOUT;  // a fill wait gave up
   if (ext0 >= SD_FINLIM) return SD_EINFEASIBLE;
   if (tb[2] != 0 || tb[0] * 4294967296LL + tb[1] != ext0) return SD_EINTERNAL;
   double cc = 0.0;

@@ -234,7 +234,7 @@ def test_bench_launch_configuration(sd, E1, par1):
         assert res[0][key] == single[key]
 
 
-@pytest.mark.parametrize("group", [8, 16, 32])
+@pytest.mark.parametrize("group", [0, 8, 16, 32])
 def test_every_group_size_gives_the_oracle_tables(sd, E1, par1, group):
     """The fill's threads-per-layer-pair choice changes speed, never results."""
     prot = inputs.random_protein(35, 31)
@@ -245,6 +245,40 @@ def test_every_group_size_gives_the_oracle_tables(sd, E1, par1, group):
     plan.run()
     compare_tables(plan, 0, o)
     compare_design(plan.results()[0], o, 4.0)
+
+
+def test_group_by_span_matches_the_oracle(sd, E1, par1):
+    """SD_GROUP_BY_SPAN switches the fill between its group-8, -16 and -32
+    instances as the spans shrink.  Nine 400-aa proteins and one 260-aa
+    protein: on a 148-SM B300 the spans hold at least 8,880 layer pairs (one
+    wave of resident group-8 blocks) up to span ~312 and at least 4,440 (one
+    wave at group 16) up to span ~723, so the 260-aa design (780 nt) is filled
+    by all three instances.  Its tables and design equal the oracle's; every
+    design equals a run at fixed group 8."""
+    import os
+    batch = inputs.protein_batch([400] * 9 + [260], seed=123)
+    prots = [b[0] for b in batch]
+    ws = np.stack([b[1] for b in batch])
+    lams = [b[2] for b in batch]
+    plan = sd.Plan(E1, prots, ws, lams)
+    plan.group = sd.SD_GROUP_BY_SPAN
+    plan.run()
+    res = plan.results()
+    prev = oracle.set_threads(os.cpu_count() or 1)
+    try:
+        o = oracle.run(par1, prots[9], ws[9], lams[9])
+    finally:
+        oracle.set_threads(prev)
+    compare_tables(plan, 9, o)
+    compare_design(res[9], o, lams[9])
+    plan.free()
+    ref = sd.Plan(E1, prots, ws, lams)
+    ref.group = 8
+    ref.run()
+    keys = ("status", "mrna", "structure", "energy", "objective_fx", "Z", "retained_cells")
+    assert [tuple(r[k] for k in keys) for r in ref.results()] == \
+        [tuple(r[k] for k in keys) for r in res]
+    ref.free()
 
 
 def test_graph_replay_of_a_mixed_batch(sd, E1, par1):
@@ -286,8 +320,8 @@ def test_autotune_then_graph(sd, E1):
     args = ([b[0] for b in batch], np.stack([b[1] for b in batch]), [b[2] for b in batch])
     plan = sd.Plan(E1, *args)
     tune = plan.autotune()
-    assert sorted(tune) == [8, 16, 32] and all(v > 0 for v in tune.values())
-    assert plan.group in (8, 16, 32)
+    assert sorted(tune) == [sd.SD_GROUP_BY_SPAN, 8, 16, 32] and all(v > 0 for v in tune.values())
+    assert plan.group in (sd.SD_GROUP_BY_SPAN, 8, 16, 32)
     plan.set_graph(True)
     plan.set_timing(True)
     plan.run()
