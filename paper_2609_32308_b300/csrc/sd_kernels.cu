@@ -1190,15 +1190,35 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         }
       const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
+      // two entries per thread and round, their loads issued together (the
+      // S1 rows of the splits are far apart: more loads in flight); entries
+      // are in decreasing layer order, so the scan ends at the first entry
+      // on layer i or before
 #pragma unroll 1
-      for (int k = sub; k < cnt; k += G) {
-        const int ce = D.cand_c[off + k];
-        const int lc = ce >> SD_CAND_SHIFT;
-        if (lc <= i) break;  // entries are in decreasing layer order
-        const int64_t v = ro(D.S1 + F.cs(i, sa, lc, ce & ((1 << SD_CAND_SHIFT) - 1)));
-        if (!fin(v)) continue;
-        upd(s2, v + D.cand_B[off + k]);
-        TERM(1);
+      for (int k0 = sub; k0 < cnt; k0 += 2 * G) {
+        int ce[2];
+        bool in[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int k = k0 + u * G;
+          ce[u] = k < cnt ? D.cand_c[off + k] : 0;
+          in[u] = k < cnt && (ce[u] >> SD_CAND_SHIFT) > i;
+        }
+        int64_t v[2], cb[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          v[u] = in[u] ? ro(D.S1 + F.cs(i, sa, ce[u] >> SD_CAND_SHIFT,
+                                        ce[u] & ((1 << SD_CAND_SHIFT) - 1)))
+                       : SD_INF;
+          cb[u] = in[u] ? D.cand_B[off + k0 + u * G] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; u++)
+          if (fin(v[u])) {
+            upd(s2, v[u] + cb[u]);
+            TERM(1);
+          }
+        if (!in[1]) break;
       }
     }
     seg_min<G>(s2);
