@@ -293,18 +293,16 @@ __device__ __forceinline__ void upd6(int64_t (&qv)[6], int tm, int64_t base, int
 // (after the 5' nucleotide of the pair) to y (before its 3' nucleotide); x is
 // slot sx of layer lx, y slot sy of layer ly.  The options are split into
 // classes, and inside a class the G threads of the group take consecutive
-// entries of one flat list, so that every thread runs the same inner loops
-// (over the out-edges of x and the in-edges of y, the same for the group):
-//   hairpin        out-edges of x x in-edges of y (explicit paths for L = 3, 4, 6)
-//   stack, bulges  the states of the inner pair's moving end (l1 = 0 or l2 = 0)
-//   1 x n          out-edges of the states d of the inner pair (l1 = 1)
-//   n x 1          in-edges of the states c of the inner pair (l2 = 1, l1 >= 2)
-//   2x2, 2x3, 3x2  (in-edge of c, out-edge of d) pairs
-//   generic        out-edges of x x in-edges of y, through the IL table
-//   multiloop      one term
-// Where the loop energy splits into a part that depends on the inner pair and
-// a part that depends on the outer one, the best inner type comes from the
-// inner cell's precomputed table W.
+// entries of one list:
+//   hairpin           out-edges of x x in-edges of y (explicit paths for L = 3, 4, 6)
+//   stack, bulges     the states of the inner pair's moving end (l1 = 0 or l2 = 0);
+//                     bulges l >= 2 take the inner cell's bulge term WB
+//   1 x 1, 1 x 2      the one- and two-edge right sides into y
+//   2 x 1, 2 x 2      the two-edge left sides out of x, each with the right sides
+//   generic, 1 x n, n x 1 (long side >= 3), 2x3, 3x2
+//                     out-edges of x x in-edges of y, through the tables IL and Af
+//                     of the cell one nucleotide inside
+//   multiloop         one term
 // ---------------------------------------------------------------------------
 template <int G, bool COUNT>
 __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdParams &P,
@@ -409,88 +407,71 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
     }
     if (fin(bul)) upd6<COUNT>(qv, tm, bul, 0, ops, [&](int t) { return T.au[t]; });
   }
-  // ---- 1 x 1 and 1 x 2: l1 = 1 (nucleotide p after the outer 5' end), l2 <= 2;
-  // entries are the out-edges r1 of the inner pair's 3' end d (1 x n with
-  // l2 >= 3 comes from the factor table Af below) ----
+  // ---- 1 x 1 and 1 x 2: l1 = 1 (nucleotide p after the outer 5' end), l2 <= 2
+  // (1 x n with l2 >= 3 comes from the factor table Af below).  Entries: the
+  // in-edges r1: d -> y (l2 = 1), then the in-edges r2: u -> y, each with the
+  // in-edges r1: d -> u of its source (l2 = 2); the inner pair (c, d) needs
+  // d at least 5 layers after c ----
   {
     const int lc = lx + 1;
-    const int dlo = max(lx + 6, ly - 2), dhi = ly - 1;
-    // out-edges of the states of layers dlo..dhi (at most ly-2 and ly-1) in
-    // state order: the edges of layer dhi start at kb
-    const int dlos = F.ls(dlo), dhis = F.ls(dhi);
-    const int k0 = dlo <= dhi ? F.fo_off[dlos] : 0;
-    const int kb = dlo <= dhi ? F.fo_off[dhis] : 0;
-    const int k1 = dlo <= dhi ? F.fo_off[F.ls(dhi + 1)] : 0;
+    const int n1 = ly - 1 >= lx + 6 ? niy : 0, n2 = ly - 2 >= lx + 6 ? niy : 0;
+    const int ly2s = F.ls(ly - 2);
 #pragma unroll 1
-    for (int k = k0 + sub; k < k1; k += G) {
-      const SdFlatEdge r1 = F.fo[k];
-      const int d = r1.v, u = r1.wl >> 2, fR = r1.wl & 3;
-      const bool hi = k >= kb;
-      const int ld = hi ? dhi : dlo, ds = d - (hi ? dhis : dlos), l2 = ly - ld;
-      if (l2 == 1) {
-        if (u != y) continue;
+    for (int k = sub; k < n1 + n2; k += G) {
+      const bool one = k < n1;  // l2 = 1
+      const SdEdge er = F.in(y, one ? k : k - n1);
+      // l2 = 1: er is r1 (d = its source); l2 = 2: er is r2 (u = its source)
+      const int nr1 = one ? 1 : F.nin(er.other);
+#pragma unroll 1
+      for (int k1 = 0; k1 < nr1; k1++) {
+        const SdEdge r1 = one ? er : F.in(er.other, k1);
+        const int ds = r1.other - (one ? ly1s : ly2s), fR = r1.label;
+        const int64_t rc = one ? r1.cost : r1.cost + er.cost;
+        const int idx2 = fR * 4 + er.label;  // 1 x 2: (fR, lR)
 #pragma unroll 1
         for (int a = 0; a < nox; a++) {
           const SdEdge ec = F.out(x, a);
           const int p = ec.label, cs = ec.other - lx1s;
-          const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
-          const int64_t base = ec.cost + r1.cost;
+          const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, one ? ly - 1 : ly - 2, ds) * 6;
+          const int64_t base = ec.cost + rc;
 #pragma unroll 1
           for (int ti = 0; ti < 6; ti++) {
             const int64_t v = ro(vr + ti);
             if (!fin(v)) continue;
             const int s = rev_type(ti);
-            upd6<COUNT>(qv, tm, v + base, 3, ops, [&](int t) { return I11[t][s][p * 4 + fR]; });
-          }
-        }
-      } else {  // l2 == 2: explicit 2-edge right side
-#pragma unroll 1
-        for (int b2 = 0; b2 < F.nout(u); b2++) {
-          const SdEdge r2 = F.out(u, b2);
-          if (r2.other != y) continue;
-          const int lR = r2.label;
-#pragma unroll 1
-          for (int a = 0; a < nox; a++) {
-            const SdEdge ec = F.out(x, a);
-            const int p = ec.label, cs = ec.other - lx1s;
-            const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
-            const int64_t base = ec.cost + r1.cost + r2.cost;
-#pragma unroll 1
-            for (int ti = 0; ti < 6; ti++) {
-              const int64_t v = ro(vr + ti);
-              if (!fin(v)) continue;
-              const int s = rev_type(ti);
+            if (one)
+              upd6<COUNT>(qv, tm, v + base, 3, ops, [&](int t) { return I11[t][s][p * 4 + fR]; });
+            else
               upd6<COUNT>(qv, tm, v + base, 4, ops,
-                          [&](int t) { return I21[t][s][p * 16 + fR * 4 + lR]; });
-            }
+                          [&](int t) { return I21[t][s][p * 16 + idx2]; });
           }
         }
       }
     }
   }
-  // ---- 2 x 1: l2 = 1 (nucleotide r before the outer 3' end), l1 = 2; entries
-  // are the in-edges p2 of the inner pair's 5' end c (n x 1 with l1 >= 3 comes
-  // from Af) ----
+  // ---- 2 x 1 (l1 = 2, l2 = 1) and 2 x 2 (l1 = l2 = 2): the entries are the
+  // two-edge left sides x -> w -> c (p1, p2), by (p1, out-edge slot of w);
+  // each takes the right sides into y: the in-edges r: d -> y (2 x 1), and
+  // the in-edges r2: u -> y with the in-edges r1: d -> u of u (2 x 2)
+  // (2x3 and 3x2 come from Af) ----
   if (g >= 8) {
-    const int ld = ly - 1, lc = lx + 2;
-    const int lcs = F.ls(lc);
-    const int k0 = F.fi_off[lcs], k1 = F.fi_off[F.ls(lc + 1)];
+    const int lc = lx + 2, lcs = F.ls(lc), ly2s = F.ls(ly - 2);
 #pragma unroll 1
-    for (int k = k0 + sub; k < k1; k += G) {
-      const SdFlatEdge p2 = F.fi[k];
-      const int c = p2.v, w = p2.wl >> 2, lL = p2.wl & 3;
-      const int cs = c - lcs;
+    for (int k = sub; k < nox * SD_MAXOUT; k += G) {
+      const SdEdge p1 = F.out(x, k / SD_MAXOUT);
+      const int b = k % SD_MAXOUT;
+      if (b >= F.nout(p1.other)) continue;
+      const SdEdge p2 = F.out(p1.other, b);
+      const int cs = p2.other - lcs, fL = p1.label, lL = p2.label;
+      const int64_t lcost = p1.cost + p2.cost;
 #pragma unroll 1
-      for (int b = 0; b < niy; b++) {
-        const SdEdge er = F.in(y, b);
-        const int r = er.label, ds = er.other - ly1s;
-        const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
-#pragma unroll 1
-        for (int a = 0; a < nox; a++) {
-          const SdEdge p1 = F.out(x, a);
-          if (p1.other != w) continue;
-          const int fL = p1.label;
-          const int64_t base = er.cost + p1.cost + p2.cost;
+      for (int b2 = 0; b2 < niy; b2++) {
+        const SdEdge er = F.in(y, b2);
+        // 2 x 1: d = the source of er, on layer ly - 1
+        {
+          const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ly - 1, er.other - ly1s) * 6;
+          const int64_t base = er.cost + lcost;
+          const int r = er.label;
 #pragma unroll 1
           for (int ti = 0; ti < 6; ti++) {
             const int64_t v = ro(vr + ti);
@@ -500,48 +481,22 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
                         [&](int t) { return I21[s][t][r * 16 + fL * 4 + lL]; });
           }
         }
-      }
-    }
-  }
-  // ---- 2x2: entries are (in-edge p2 of c, out-edge r1 of d) (2x3 and 3x2 come
-  // from Af) ----
-  if (g >= 9) {
-    const int lc = lx + 2, ld = ly - 2;
-    const int lcs = F.ls(lc), lds = F.ls(ld), lc1s = F.ls(lc - 1), ld1s = F.ls(ld + 1);
-    const int pi0 = F.fi_off[lcs], npi = F.fi_off[F.ls(lc + 1)] - pi0;
-    const int ro0 = F.fo_off[lds], nro = F.fo_off[F.ls(ld + 1)] - ro0;
+        // 2 x 2: er is r2 (u = its source), d -> u on layer ly - 2
+        if (g >= 9) {
+          const int u = er.other;
 #pragma unroll 1
-    for (int k = sub; k < npi * nro; k += G) {
-      const int kp = k / nro, kr = k - kp * nro;
-      const SdFlatEdge p2 = F.fi[pi0 + kp], r1 = F.fo[ro0 + kr];
-      const int cs = p2.v - lcs, ds = r1.v - lds;
-      const int w = p2.wl >> 2, lL = p2.wl & 3, u = r1.wl >> 2, fR = r1.wl & 3;
-      const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ld, ds) * 6;
-      int fm = 0;  // the inner types with a finite V
-      {
-        int64_t vv[6];
-        F.v6(F.cs(lc, cs, ld, ds), vv);
-#pragma unroll
-        for (int ti = 0; ti < 6; ti++) fm |= (int)fin(vv[ti]) << ti;
-      }
-      if (!fm) continue;
+          for (int b1 = 0; b1 < F.nin(u); b1++) {
+            const SdEdge r1 = F.in(u, b1);
+            const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ly - 2, r1.other - ly2s) * 6;
+            const int64_t hc = lcost + r1.cost + er.cost;
+            const int idx = fL * 64 + lL * 16 + r1.label * 4 + er.label;
 #pragma unroll 1
-      for (int a = 0; a < nox; a++) {
-        const SdEdge p1 = F.out(x, a);
-        const int64_t hl = F.Hh(lx + 1, p1.other - lx1s, lc - 1, w - lc1s);
-        if (!fin(hl)) continue;
-#pragma unroll 1
-        for (int b2 = 0; b2 < niy; b2++) {
-          const SdEdge r2 = F.in(y, b2);
-          const int64_t hr = F.Hh(ld + 1, u - ld1s, ly - 1, r2.other - ly1s);
-          if (!fin(hr)) continue;
-          const int64_t hc = p1.cost + p2.cost + r1.cost + r2.cost + hl + hr;
-          const int idx = p1.label * 64 + lL * 16 + fR * 4 + r2.label;
-#pragma unroll 1
-          for (int ti = 0; ti < 6; ti++) {
-            if (!((fm >> ti) & 1)) continue;
-            const int s = rev_type(ti);
-            upd6<COUNT>(qv, tm, ro(vr + ti) + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
+            for (int ti = 0; ti < 6; ti++) {
+              const int64_t v = ro(vr + ti);
+              if (!fin(v)) continue;
+              const int s = rev_type(ti);
+              upd6<COUNT>(qv, tm, v + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
+            }
           }
         }
       }
