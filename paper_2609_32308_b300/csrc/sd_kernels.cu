@@ -1363,16 +1363,14 @@ __global__ void __launch_bounds__(256) k_exterior(const SdDesign *__restrict__ d
         const int64_t x = D.Ext[e.other];
         if (fin(x)) upd(bv, x + e.cost);
       }
-      for (int b = G.lstart(k + 1) + threadIdx.x; b < N; b += blockDim.x) {
-        const int lb = G.layer(b);
-        if (lb - k < 5) continue;
+      // a branch (a, b): min over t of V_t + AU(t) = B(a, b) - ML_intern
+      // (Eq. branch adds the same ML_intern to every type)
+      const int64_t mli = fx(P.mlintern);
+      for (int b = G.lstart(min(k + 5, n + 1)) + threadIdx.x; b < N; b += blockDim.x) {
         const int64_t eb = D.Ext[b];
         if (!fin(eb)) continue;
-        const int64_t cs = G.slot(a, b, k, lb) * 6;
-        for (int t = 0; t < 6; t++) {
-          const int64_t v = D.V[cs + t];
-          if (fin(v)) upd(bv, v + fx(P.au[t]) + eb);
-        }
+        const int64_t bb = D.Bv[G.slot(a, b, k, G.layer(b))];
+        if (fin(bb)) upd(bv, bb - mli + eb);
       }
       warp_min(bv);
       if (lane == 0) smv[w] = bv;
