@@ -1345,42 +1345,62 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
 // ---------------------------------------------------------------------------
 // exterior suffix values (Sec. 5 final-column exterior DP), one block per design
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_exterior(const SdDesign *__restrict__ designs,
-                                                  const SdParams *__restrict__ Pp) {
+#ifndef SD_EXT_THREADS
+#define SD_EXT_THREADS 1024
+#endif
+__global__ void __launch_bounds__(SD_EXT_THREADS) k_exterior(const SdDesign *__restrict__ designs,
+                                                             const SdParams *__restrict__ Pp) {
   const SdDesign &D = designs[blockIdx.x];
   const SdParams &P = *Pp;
-  __shared__ int64_t smv[8];
+  __shared__ int64_t smv[SD_EXT_THREADS / 32][SD_W];
   Lat G(D);
   const int n = D.n, N = D.N;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // a branch (a, b): min over t of V_t + AU(t) = B(a, b) - ML_intern (Eq.
+  // branch adds the same ML_intern to every type)
+  const int64_t mli = fx(P.mlintern);
   if (threadIdx.x == 0) D.Ext[N - 1] = 0;
   __syncthreads();
+  // layer by layer from the end, every state of the layer at once
   for (int k = n - 1; k >= 0; k--) {
-    for (int a = G.lstart(k); a < G.lstart(k + 1); a++) {
-      int64_t bv = SD_INF;
-      if ((int)threadIdx.x < G.nout(a)) {
-        const SdEdge e = G.out(a, threadIdx.x);
+    const int a0 = G.lstart(k), wa = G.lstart(k + 1) - a0;
+    int64_t bv[SD_W];
+#pragma unroll
+    for (int s = 0; s < SD_W; s++) bv[s] = SD_INF;
+    // unpaired: the out-edges of the layer's states, one per thread
+    if ((int)threadIdx.x < wa * SD_MAXOUT) {
+      const int sa = threadIdx.x / SD_MAXOUT, q = threadIdx.x % SD_MAXOUT;
+      if (q < G.nout(a0 + sa)) {
+        const SdEdge e = G.out(a0 + sa, q);
         const int64_t x = D.Ext[e.other];
-        if (fin(x)) upd(bv, x + e.cost);
+#pragma unroll
+        for (int s = 0; s < SD_W; s++)
+          if (s == sa && fin(x)) upd(bv[s], x + e.cost);
       }
-      // a branch (a, b): min over t of V_t + AU(t) = B(a, b) - ML_intern
-      // (Eq. branch adds the same ML_intern to every type)
-      const int64_t mli = fx(P.mlintern);
-      for (int b = G.lstart(min(k + 5, n + 1)) + threadIdx.x; b < N; b += blockDim.x) {
-        const int64_t eb = D.Ext[b];
-        if (!fin(eb)) continue;
-        const int64_t bb = D.Bv[G.slot(a, b, k, G.layer(b))];
-        if (fin(bb)) upd(bv, bb - mli + eb);
-      }
-      warp_min(bv);
-      if (lane == 0) smv[w] = bv;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int q = 1; q < (int)(blockDim.x >> 5); q++) upd(bv, smv[q]);
-        D.Ext[a] = settle(bv);
-      }
-      __syncthreads();
     }
+    for (int b = G.lstart(min(k + 5, n + 1)) + threadIdx.x; b < N; b += blockDim.x) {
+      const int64_t eb = D.Ext[b];
+      if (!fin(eb)) continue;
+      const int lb = G.layer(b);
+#pragma unroll
+      for (int s = 0; s < SD_W; s++)
+        if (s < wa) {
+          const int64_t bb = D.Bv[G.slot(a0 + s, b, k, lb)];
+          if (fin(bb)) upd(bv[s], bb - mli + eb);
+        }
+    }
+#pragma unroll
+    for (int s = 0; s < SD_W; s++) {
+      warp_min(bv[s]);
+      if (lane == 0) smv[w][s] = bv[s];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < wa) {
+      int64_t v = SD_INF;
+      for (int q = 0; q < (int)(blockDim.x >> 5); q++) upd(v, smv[q][threadIdx.x]);
+      D.Ext[a0 + threadIdx.x] = settle(v);
+    }
+    __syncthreads();
   }
 }
 
@@ -1404,7 +1424,10 @@ __global__ void __launch_bounds__(256) k_exterior(const SdDesign *__restrict__ d
 // many options (exterior branches, two-loops, candidate splits) use the whole
 // block and a block-wide minimum of the option's position in the order.
 // ---------------------------------------------------------------------------
-constexpr int TB_THREADS = 256;
+#ifndef SD_TB_THREADS
+#define SD_TB_THREADS 1024
+#endif
+constexpr int TB_THREADS = SD_TB_THREADS;
 constexpr unsigned long long NO_OPTION = ~0ull;
 
 __device__ unsigned long long block_min(unsigned long long v, unsigned long long *red) {
@@ -1756,31 +1779,36 @@ __global__ void __launch_bounds__(TB_THREADS) k_traceback(const SdDesign *__rest
     __syncthreads();
     if (c0 == 0) break;
     if (c0 == 1) continue;
-    // branch (b ascending, type) with V_t(a,b) + AU(t) + Ext(b) = Ext(a)
+    // branch (b ascending, type) with V_t(a,b) + AU(t) + Ext(b) = Ext(a): the
+    // smallest b with B(a,b) - ML_intern + Ext(b) = Ext(a) (B - ML_intern is
+    // the minimum over t of V_t + AU(t)), then its smallest attaining type
     unsigned long long best = NO_OPTION;
     const int la = G.layer(a);
-    const int64_t v = D.Ext[a];
-    for (int b = G.lstart(la + 1) + threadIdx.x; b < N; b += TB_THREADS) {
-      const int lb = G.layer(b);
-      if (lb - la < 5) continue;
+    const int64_t v = D.Ext[a], mli = fx(P.mlintern);
+    for (int b = G.lstart(min(la + 5, D.n + 1)) + threadIdx.x; b < N; b += TB_THREADS) {
       const int64_t eb = D.Ext[b];
       if (!fin(eb)) continue;
-      const int64_t cs = G.slot(a, b, la, lb) * 6;
-      for (int t = 0; t < 6; t++) {
-        const int64_t x = D.V[cs + t];
-        if (fin(x) && x + fx(P.au[t]) + eb == v) {
-          const unsigned long long pos = (unsigned long long)b * 8 + t;
-          best = pos < best ? pos : best;
-          break;
-        }
+      const int64_t bb = D.Bv[G.slot(a, b, la, G.layer(b))];
+      if (fin(bb) && bb - mli + eb == v) {
+        best = (unsigned long long)b;
+        break;  // this thread's later b are larger
       }
     }
     best = block_min(best, red);
     if (t0) {
-      if (best == NO_OPTION) {
+      int t = -1;
+      if (best != NO_OPTION) {
+        const int b = (int)best;
+        const int64_t eb = D.Ext[b], cs = G.slot(a, b, la, G.layer(b)) * 6;
+        for (int q = 0; q < 6 && t < 0; q++) {
+          const int64_t x = D.V[cs + q];
+          if (fin(x) && x + fx(P.au[q]) + eb == v) t = q;
+        }
+      }
+      if (t < 0) {
         tb.err = 15;
       } else {
-        const int b = (int)(best >> 3), t = (int)(best & 7);
+        const int b = (int)best;
         tb.energy += P.au[t];
         tb.push(1, a, b, t);
         a = b;
@@ -2228,7 +2256,7 @@ extern "C" int SD_KFN(sd_k_run)(const SdDesign *d_designs, int count, const int 
   if (events) record(events[0], st);
   if (launch_fill<false>(group, d_designs, count, ns, d_cpre, d_params, st, nullptr)) return -1;
   if (events) record(events[1], st);
-  k_exterior<<<count, 256, 0, st>>>(d_designs, d_params);
+  k_exterior<<<count, SD_EXT_THREADS, 0, st>>>(d_designs, d_params);
   if (events) record(events[2], st);
   k_traceback<<<count, TB_THREADS, 0, st>>>(d_designs, d_params);
   if (events) record(events[3], st);
