@@ -258,6 +258,33 @@ struct alignas(16) GapStage {
   int64_t hl[SD_GAPW][SD_SLOTS], hr[SD_GAPW][SD_SLOTS];
 };
 
+// A V row of an earlier span (read-only path), or of this span: the values
+// and the mask of the finite types (bit t for a finite V_t).  The type loops
+// then visit the finite types only (most pairs admit one or two), picking
+// each value by constant-index selects.
+template <bool CUR>
+__device__ __forceinline__ int vrow(const int64_t *vr, int64_t (&v)[6]) {
+  const longlong2 *p = reinterpret_cast<const longlong2 *>(vr);
+  const longlong2 a = CUR ? p[0] : ro(p), b = CUR ? p[1] : ro(p + 1), c = CUR ? p[2] : ro(p + 2);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+  v[4] = c.x;
+  v[5] = c.y;
+  int fm = 0;
+#pragma unroll
+  for (int t = 0; t < 6; t++) fm |= (int)fin(v[t]) << t;
+  return fm;
+}
+__device__ __forceinline__ int64_t pick6(const int64_t (&v)[6], int t) {
+  int64_t r = v[0];
+#pragma unroll
+  for (int q = 1; q < 6; q++)
+    if (t == q) r = v[q];
+  return r;
+}
+
 // the type of the same pair read from the other strand (AU <-> UA, CG <-> GC,
 // GU <-> UG)
 __device__ __forceinline__ int rev_type(int t) { return t < 4 ? 3 - t : 9 - t; }
@@ -396,12 +423,10 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
         const int vc = right ? F.cs(lx, sx, lv, sv) : F.cs(lv, sv, ly, sy);
         const int64_t *vr = F.V + (int64_t)vc * 6;
         const int64_t e1 = h + fx(l == 1 ? T.bulge[1] : 0);
-#pragma unroll 1
-        for (int ti = 0; ti < 6; ti++) {
-          const int64_t v = l == 0 ? vr[ti] : ro(vr + ti);
-          if (!fin(v)) continue;
-          const int s = rev_type(ti);
-          upd6<COUNT>(qv, tm, v + e1, 2, ops, [&](int t) { return T.stack[t][s]; });
+        int64_t vv[6];
+        for (int fm = l == 0 ? vrow<true>(vr, vv) : vrow<false>(vr, vv); fm; fm &= fm - 1) {
+          const int ti = __ffs(fm) - 1, s = rev_type(ti);
+          upd6<COUNT>(qv, tm, pick6(vv, ti) + e1, 2, ops, [&](int t) { return T.stack[t][s]; });
         }
       }
     }
@@ -434,11 +459,10 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
           const int p = ec.label, cs = ec.other - lx1s;
           const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, one ? ly - 1 : ly - 2, ds) * 6;
           const int64_t base = ec.cost + rc;
-#pragma unroll 1
-          for (int ti = 0; ti < 6; ti++) {
-            const int64_t v = ro(vr + ti);
-            if (!fin(v)) continue;
-            const int s = rev_type(ti);
+          int64_t vv[6];
+          for (int fm = vrow<false>(vr, vv); fm; fm &= fm - 1) {
+            const int ti = __ffs(fm) - 1, s = rev_type(ti);
+            const int64_t v = pick6(vv, ti);
             if (one)
               upd6<COUNT>(qv, tm, v + base, 3, ops, [&](int t) { return I11[t][s][p * 4 + fR]; });
             else
@@ -472,12 +496,10 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
           const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ly - 1, er.other - ly1s) * 6;
           const int64_t base = er.cost + lcost;
           const int r = er.label;
-#pragma unroll 1
-          for (int ti = 0; ti < 6; ti++) {
-            const int64_t v = ro(vr + ti);
-            if (!fin(v)) continue;
-            const int s = rev_type(ti);
-            upd6<COUNT>(qv, tm, v + base, 4, ops,
+          int64_t vv[6];
+          for (int fm = vrow<false>(vr, vv); fm; fm &= fm - 1) {
+            const int ti = __ffs(fm) - 1, s = rev_type(ti);
+            upd6<COUNT>(qv, tm, pick6(vv, ti) + base, 4, ops,
                         [&](int t) { return I21[s][t][r * 16 + fL * 4 + lL]; });
           }
         }
@@ -490,12 +512,10 @@ __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdP
             const int64_t *vr = F.V + (int64_t)F.cs(lc, cs, ly - 2, r1.other - ly2s) * 6;
             const int64_t hc = lcost + r1.cost + er.cost;
             const int idx = fL * 64 + lL * 16 + r1.label * 4 + er.label;
-#pragma unroll 1
-            for (int ti = 0; ti < 6; ti++) {
-              const int64_t v = ro(vr + ti);
-              if (!fin(v)) continue;
-              const int s = rev_type(ti);
-              upd6<COUNT>(qv, tm, v + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
+            int64_t vv[6];
+            for (int fm = vrow<false>(vr, vv); fm; fm &= fm - 1) {
+              const int ti = __ffs(fm) - 1, s = rev_type(ti);
+              upd6<COUNT>(qv, tm, pick6(vv, ti) + hc, 8, ops, [&](int t) { return P.int22[t][s][idx]; });
             }
           }
         }
