@@ -48,7 +48,6 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __constant__ int c_pair5[6] = {0, 1, 2, 3, 2, 3};
 __constant__ int c_pair3[6] = {3, 2, 1, 0, 3, 2};
-__constant__ int c_rev[6] = {3, 2, 1, 0, 5, 4};
 
 __device__ __forceinline__ int64_t fx(int e) { return (int64_t)e * 4294967296LL; }
 
@@ -289,13 +288,18 @@ __device__ __forceinline__ int64_t pick6(const int64_t (&v)[6], int t) {
 // GU <-> UG)
 __device__ __forceinline__ int rev_type(int t) { return t < 4 ? 3 - t : 9 - t; }
 
-// minimum over the inner pair types of vv[ti] + tab[rev ti][idx]
+// minimum over the inner pair types of vv[ti] + tab[rev ti][idx] (the finite
+// types only)
 __device__ __forceinline__ int64_t best_inner(const int64_t (&vv)[6], const int32_t (*tab)[16],
                                               int idx) {
-  int64_t bv = SD_INF;
+  int fm = 0;
 #pragma unroll
-  for (int ti = 0; ti < 6; ti++)
-    if (fin(vv[ti])) upd(bv, vv[ti] + fx(tab[c_rev[ti]][idx]));
+  for (int t = 0; t < 6; t++) fm |= (int)fin(vv[t]) << t;
+  int64_t bv = SD_INF;
+  for (; fm; fm &= fm - 1) {
+    const int ti = __ffs(fm) - 1;
+    upd(bv, pick6(vv, ti) + fx(tab[rev_type(ti)][idx]));
+  }
   return bv;
 }
 
