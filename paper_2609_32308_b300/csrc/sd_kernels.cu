@@ -1001,26 +1001,38 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
         if (ok && g >= 7 && ulo <= uhi) {
           const int a = a0 + k, im = D.in_mask[a];
+          const int uend = F.ls(uhi + 1);
+          // 2 states per thread and round, their loads issued together
 #pragma unroll 1
-          for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
-            const int pu = __ldg(&D.pos[u]);
-            const int lu = pu >> SD_CAND_SHIFT, us = pu & ((1 << SD_CAND_SHIFT) - 1), l2 = j + 2 - lu;
-            const int64_t h0 = GS.hr[j - lu][us * SD_W], h1 = GS.hr[j - lu][us * SD_W + 1];
-            if (!fin(h0) && !fin(h1)) continue;
-            const int64_t e = fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
-            const int64_t *xc =
-                D.Xc + ((int64_t)a * 4 * SD_XSPAN + ((lu - i) & (SD_XSPAN - 1))) * SD_W + us;
+          for (int u = F.ls(ulo) + sub; u < uend; u += 2 * G) {
+            int64_t h0[2], h1[2], e[2], x[2][4];
 #pragma unroll
-            for (int p = 0; p < 4; p++)
-              if ((im >> p) & 1) {
-                const int64_t x = ro(xc + p * SD_XSPAN * SD_W);
-                if (!fin(x)) continue;
-                if (fin(h0)) {
-                  upd(acc[p], x + h0 + e);
+            for (int v = 0; v < 2; v++) {
+              const int uu = u + v * G;
+              const bool in = uu < uend;
+              const int pu = in ? __ldg(&D.pos[uu]) : 0;
+              const int lu = pu >> SD_CAND_SHIFT, us = pu & ((1 << SD_CAND_SHIFT) - 1), l2 = j + 2 - lu;
+              h0[v] = in ? GS.hr[j - lu][us * SD_W] : SD_INF;
+              h1[v] = in ? GS.hr[j - lu][us * SD_W + 1] : SD_INF;
+              e[v] = in ? fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1))) : 0;
+              const bool any = fin(h0[v]) || fin(h1[v]);
+              const int64_t *xc =
+                  D.Xc + ((int64_t)a * 4 * SD_XSPAN + ((lu - i) & (SD_XSPAN - 1))) * SD_W + us;
+#pragma unroll
+              for (int p = 0; p < 4; p++)
+                x[v][p] = any && ((im >> p) & 1) ? ro(xc + p * SD_XSPAN * SD_W) : SD_INF;
+            }
+#pragma unroll
+            for (int v = 0; v < 2; v++)
+#pragma unroll
+              for (int p = 0; p < 4; p++) {
+                if (!fin(x[v][p])) continue;
+                if (fin(h0[v])) {
+                  upd(acc[p], x[v][p] + h0[v] + e[v]);
                   TERM(2);
                 }
-                if (fin(h1)) {
-                  upd(acc[4 + p], x + h1 + e);
+                if (fin(h1[v])) {
+                  upd(acc[4 + p], x[v][p] + h1[v] + e[v]);
                   TERM(2);
                 }
               }
@@ -1040,26 +1052,38 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
         const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
         if (ok && g >= 7 && wlo <= whi) {
           const int b = b0 + k, om = D.out_mask[b];
+          const int wend = F.ls(whi + 1);
+          // 2 states per thread and round, their loads issued together
 #pragma unroll 1
-          for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
-            const int pw = __ldg(&D.pos[w]);
-            const int lw = pw >> SD_CAND_SHIFT, ws = pw & ((1 << SD_CAND_SHIFT) - 1), l1 = lw - i + 2;
-            const int64_t h0 = GS.hl[lw - i][ws * SD_W], h1 = GS.hl[lw - i][ws * SD_W + 1];
-            if (!fin(h0) && !fin(h1)) continue;
-            const int64_t e = fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
-            const int64_t *yr =
-                D.Yr + ((int64_t)b * 4 * SD_XSPAN + ((j - lw) & (SD_XSPAN - 1))) * SD_W + ws;
+          for (int w = F.ls(wlo) + sub; w < wend; w += 2 * G) {
+            int64_t h0[2], h1[2], e[2], y[2][4];
 #pragma unroll
-            for (int r = 0; r < 4; r++)
-              if ((om >> r) & 1) {
-                const int64_t y = ro(yr + r * SD_XSPAN * SD_W);
-                if (!fin(y)) continue;
-                if (fin(h0)) {
-                  upd(acc[r], y + h0 + e);
+            for (int v = 0; v < 2; v++) {
+              const int ww = w + v * G;
+              const bool in = ww < wend;
+              const int pw = in ? __ldg(&D.pos[ww]) : 0;
+              const int lw = pw >> SD_CAND_SHIFT, ws = pw & ((1 << SD_CAND_SHIFT) - 1), l1 = lw - i + 2;
+              h0[v] = in ? GS.hl[lw - i][ws * SD_W] : SD_INF;
+              h1[v] = in ? GS.hl[lw - i][ws * SD_W + 1] : SD_INF;
+              e[v] = in ? fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1))) : 0;
+              const bool any = fin(h0[v]) || fin(h1[v]);
+              const int64_t *yr =
+                  D.Yr + ((int64_t)b * 4 * SD_XSPAN + ((j - lw) & (SD_XSPAN - 1))) * SD_W + ws;
+#pragma unroll
+              for (int r = 0; r < 4; r++)
+                y[v][r] = any && ((om >> r) & 1) ? ro(yr + r * SD_XSPAN * SD_W) : SD_INF;
+            }
+#pragma unroll
+            for (int v = 0; v < 2; v++)
+#pragma unroll
+              for (int r = 0; r < 4; r++) {
+                if (!fin(y[v][r])) continue;
+                if (fin(h0[v])) {
+                  upd(acc[r], y[v][r] + h0[v] + e[v]);
                   TERM(2);
                 }
-                if (fin(h1)) {
-                  upd(acc[4 + r], y + h1 + e);
+                if (fin(h1[v])) {
+                  upd(acc[4 + r], y[v][r] + h1[v] + e[v]);
                   TERM(2);
                 }
               }
