@@ -51,8 +51,8 @@ ENERGY_SEED = 1
 # layer pair, from a one-launch ncu capture of a small case of the kernel
 # source with this SHA-256, scaled here to a bench launch by its layer pairs
 # (the procedure is in the design notes).  Any other kernel source: null.
-FILL_DRAM = {"sha256": "4c44aaf09328ef71639459cc80fa113c4e273d35ff6aeec2bdbb854ed6e32905",
-             "bytes_per_layer_pair": 158474752 / 14416}
+FILL_DRAM = {"sha256": "5b4e96c07bdda9f31fbd16228de22a953cfca96d02d7608f6e2e892bf6adb9d7",
+             "bytes_per_layer_pair": (144448000 + 12864256) / 14416}
 
 
 def parse():
