@@ -1180,17 +1180,28 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     const int sa = ok ? k / wb : 0, sb = ok ? k % wb : 0, s = sa * SD_W + sb;
     const int a = a0 + sa, b = b0 + sb;
     const int cell = ok ? F.cs(i, sa, j, sb) : 0;
-    int64_t s2 = SD_INF;
+    int64_t s2 = SD_INF, ps = SD_INF;
     if (ok) {
-      if (g >= 2)
+      // one unpaired edge at either end: the out-edges of a (P_S), then the
+      // in-edges of b (P_S and the edge extensions of S2), split over the group
+      if (g >= 2) {
+        const int noa = F.nout(a), nt = noa + F.nin(b);
 #pragma unroll 1
-        for (int k = sub; k < F.nin(b); k += G) {
-          const SdEdge e = F.in(b, k);
-          const int64_t v = ro(D.S2 + F.cs(i, sa, j - 1, e.other - js));
-          if (!fin(v)) continue;
-          upd(s2, v + e.cost + mlb);
-          TERM(2);
+        for (int k = sub; k < nt; k += G) {
+          const bool left = k < noa;
+          const SdEdge e = left ? F.out(a, k) : F.in(b, k - noa);
+          const int c = left ? F.cs(i + 1, e.other - i1s, j, sb) : F.cs(i, sa, j - 1, e.other - js);
+          const int64_t v1 = ro(D.S1 + c), v2 = left ? SD_INF : ro(D.S2 + c);
+          if (fin(v1)) {
+            upd(ps, v1 + e.cost + mlb);
+            TERM(2);
+          }
+          if (fin(v2)) {
+            upd(s2, v2 + e.cost + mlb);
+            TERM(2);
+          }
         }
+      }
       const int cnt = D.cand_cap ? min(D.cand_cnt[b], __ldg(&D.cand_cap[b])) : D.cand_cnt[b];
       const int64_t off = D.cand_off[b];
       // two entries per thread and round, their loads issued together (the
@@ -1226,22 +1237,7 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     }
     seg_min<G>(s2);
     s2 = settle(s2);
-    // P_S (Eq. partitionable with S): S2 or one unpaired edge at either end,
-    // the group's threads taking the out-edges of a, then the in-edges of b
-    int64_t ps = SD_INF;
-    if (ok && g >= 2) {
-      const int noa = F.nout(a), nt = noa + F.nin(b);
-#pragma unroll 1
-      for (int k = sub; k < nt; k += G) {
-        const bool left = k < noa;
-        const SdEdge e = left ? F.out(a, k) : F.in(b, k - noa);
-        const int64_t v = ro(D.S1 + (left ? F.cs(i + 1, e.other - i1s, j, sb)
-                                         : F.cs(i, sa, j - 1, e.other - js)));
-        if (!fin(v)) continue;
-        upd(ps, v + e.cost + mlb);
-        TERM(2);
-      }
-    }
+    // P_S (Eq. partitionable with S): S2 or one unpaired edge at either end
     seg_min<G>(ps);
     if (ok && sub == 0) {
       D.S2[cell] = s2;
