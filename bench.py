@@ -71,6 +71,9 @@ def parse():
                     help="batch sizes of the 925-aa sweep (extras)")
     ap.add_argument("--mixed", type=int, default=512,
                     help="proteins of the mixed-length batch (extras; 0 = skip)")
+    ap.add_argument("--streams", type=int, default=0,
+                    help="concurrent streams of the batch (0: the faster of 1 and 2, "
+                         "tried in the warm-up)")
     ap.add_argument("--no-predictor", action="store_true",
                     help="worst-case candidate room instead of the predictor's")
     ap.add_argument("--dense-control", action="store_true",
@@ -488,6 +491,18 @@ def main():
     tune = plan.autotune()                     # 4 warm-up steps
     plan.set_graph(True)
     plan.set_timing(True)
+    # concurrent streams (designs split longest predicted work first): one or
+    # two, whichever replays faster, unless --streams fixes the count (two
+    # more warm-up steps per count tried; one stream is always run first, for
+    # the per-kernel phase times)
+    stream_ms, phase1 = {}, None
+    for k in ((1, 2) if args.streams == 0 else (1, args.streams) if args.streams > 1 else (1,)):
+        plan.streams = k
+        plan.run(stream)
+        stream_ms[k] = 1000.0 * timed_runs(plan, stream, 1)
+        if k == 1:
+            phase1 = plan.phase_times()   # per-kernel phases of one launch sequence
+    plan.streams = min(stream_ms, key=stream_ms.get) if args.streams == 0 else args.streams
     for _ in range(max(0, args.warmup - 4)):
         plan.run(stream)
     # a presized list that overflowed is regrown here, before the timed steps
@@ -538,9 +553,14 @@ def main():
     value = job_rate(args.batch, world, args.steps, elapsed)
     cell_rate = cells * world * args.steps / elapsed
     launches = plan.launches * args.steps
-    phase = [statistics.mean(x[k] for x in phases) for k in range(3)]
+    # with several streams the phase events cover the whole run only: the
+    # per-kernel phases (and the fill time of the roofline) come from the
+    # single-stream warm-up step then
+    phase = ([statistics.mean(x[k] for x in phases) for k in range(3)] if plan.streams == 1
+             else list(phase1))
     device_bytes = plan.device_bytes
     group = plan.group
+    streams = plan.streams
     ops = int(plan.count_ops().sum())          # algorithmic INT32 slots of one fill
     fill_launches = max(r["n"] for r in res)
     layer_pairs = sum(r["n"] * (r["n"] + 1) // 2 for r in res)
@@ -623,6 +643,7 @@ def main():
                        "batch": args.batch, "length_aa": args.length, "lambda": LAMBDA,
                        "fill_group": group,
                        "autotune_fill_ms": tune,
+                       "streams": streams, "streams_step_ms": stream_ms,
                        "predictor": None if pred is None else
                        {"candidate_room": room, "candidate_room_worst_case": room_worst,
                         "regrows": regrows, "margin": 2.0},
@@ -634,7 +655,9 @@ def main():
             "plain_autotune_fill_ms": plain_tune,
             "plain_designs_per_s_at_batch_group": plain_at_batch_group,
             "batched_over_plain": value / plain_value,
-            "phase_ms": {"fill": phase[0], "exterior": phase[1], "traceback": phase[2]},
+            "phase_ms": {"fill": phase[0], "exterior": phase[1], "traceback": phase[2],
+                         "source": "timed steps" if streams == 1 else
+                         "single-stream warm-up step (the timed steps ran on several streams)"},
             "measured_alu_peaks_tops": {"int32_addmin": peaks[32] / 1e12,
                                         "int64_addmin": peaks[64] / 1e12},
             "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e}
