@@ -50,3 +50,15 @@ def test_noalloc_refuses_designs_larger_than_its_scratch(sd, par1):
     small = inputs.random_protein(12, 74)
     w = inputs.random_codon_weights(74)
     assert sd.sd_design_noalloc(E, small, w, 1.0)["mrna"] == sd.sd_design(E, small, w, 1.0)["mrna"]
+
+
+def test_noalloc_edge_sizes(sd, par1):
+    """The empty protein, one codon, a stop codon alone and two codons give
+    exactly what sd_design gives."""
+    E = sd.sd_load_energy(par1)
+    w = inputs.random_codon_weights(75)
+    for prot in ("", "M", "*", "MW"):
+        got = sd.sd_design_noalloc(E, prot, w, 4.0)
+        ref = sd.sd_design(E, prot, w, 4.0)
+        for key in ("status", "mrna", "structure", "energy", "objective_fx", "n"):
+            assert got[key] == ref[key], (prot, key)
