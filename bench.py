@@ -417,6 +417,20 @@ def extras(sd, E, stream, pred, args):
         "same_designs": same}
     out["envelope_300aa_lambda_0_8"] = {"lines": len(lines), "seconds": t_env,
                                         "breakpoints": breaks[:8]}
+    # forbidden motifs (six restriction / polyadenylation-like sites): the
+    # product lattice runs on the wide fill instance; one 300-aa protein
+    motifs = ["GAAUUC", "GGAUCC", "AAGCUU", "CUCGAG", "CCCGGG", "AAUAAA"]
+    sd.sd_design_motifs(E, inputs.random_protein(60, 779), w, LAMBDA, motifs)  # warm-up
+    t0 = time.perf_counter()
+    rm = sd.sd_design_motifs(E, prot300, w300, LAMBDA, motifs)
+    t_mot = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rp = sd.sd_design(E, prot300, w300, LAMBDA)
+    t_plain1 = time.perf_counter() - t0
+    out["motifs_300aa_6_sites"] = {
+        "seconds": t_mot, "plain_seconds": t_plain1, "states": rm["states"],
+        "plain_states": rp["states"], "motif_free": not any(m in rm["mrna"] for m in motifs),
+        "objective_cost_dcal": (rm["objective_fx"] - rp["objective_fx"]) / 2 ** 32}
     # mixed lengths: log-uniform 50-1,000 aa, lambda in {0, 4} with p = 1/2,
     # per-protein weights; one graph-captured launch sequence vs the predicted
     # schedule (designs over 4 streams, longest predicted work first)
