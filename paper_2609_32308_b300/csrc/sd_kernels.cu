@@ -249,12 +249,18 @@ struct Fv {
   }
 };
 
-// Gap values of the two ends of a layer pair, staged in shared memory per
-// group: hl[l][c*W + s] = H(slot s of layer i -> slot c of layer i+l),
-// hr[l][c*W + s] = H(slot c of layer j-l -> slot s of layer j), l < SD_GAPW;
-// the two-loop options read them many times.
+// Gap values of the two ends of a layer pair: hl[l][c*W + s] = H(slot s of
+// layer i -> slot c of layer i+l), hr[l][c*W + s] = H(slot c of layer j-l ->
+// slot s of layer j), l < SD_GAPW; the two-loop options read them many
+// times.  Narrow layers stage them in shared memory per group; wide layers
+// (64 slots, 31 KB per layer pair) read the gap mirrors in global memory, so
+// that more groups fit on an SM.
 struct alignas(16) GapStage {
-  int64_t hl[SD_GAPW][SD_SLOTS], hr[SD_GAPW][SD_SLOTS];
+  int64_t hl[SD_W == 2 ? SD_GAPW : 1][SD_SLOTS], hr[SD_W == 2 ? SD_GAPW : 1][SD_SLOTS];
+};
+struct GapRows {
+  const int64_t (*hl)[SD_SLOTS];
+  const int64_t (*hr)[SD_SLOTS];
 };
 
 // A V row of an earlier span (read-only path), or of this span: the values
@@ -339,7 +345,7 @@ template <int G, bool COUNT>
 __device__ __forceinline__ void q_slot(const Fv &F, const SdDesign &D, const SdParams &P,
                                        const SmallTables &T, int sub, int x, int y, int lx,
                                        int sx, int ly, int sy, int tm, int64_t (&qv)[6],
-                                       unsigned long long &ops, const GapStage &GS) {
+                                       unsigned long long &ops, const GapRows &GS) {
   const int g = ly - lx;
   const int nox = F.nout(x), niy = F.nin(y);
   // (the 1x1 / 1x2 tables stay in global memory: a larger shared-memory
@@ -710,13 +716,22 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
   const int64_t mlb = fx(T.mlbase);
   const int js = active ? F.ls(j - 1) : 0;  // first state on layer j-1
   const int i1s = active ? F.ls(i + 1) : 0;
-  GapStage &GS = s_gap[threadIdx.x / G];
+  GapStage &GSt = s_gap[threadIdx.x / G];
   // The gap mirrors of layer i (from the left) and layer j (from the right),
   // one contiguous row each, copied into the group's stage by two bulk
   // asynchronous copies that one thread issues and a transaction barrier
   // tracks.  Entries of spans >= g still hold the +inf of the run's reset (the
   // mirrors of span l are written by the launch of span l).
-  if (!stage_gap_rows(D, active, sub, i, j, GS, s_bar[threadIdx.x / G])) return;
+  GapRows GS;
+  if constexpr (SD_W == 2) {
+    if (!stage_gap_rows(D, active, sub, i, j, GSt, s_bar[threadIdx.x / G])) return;
+    GS = GapRows{GSt.hl, GSt.hr};
+  } else {
+    const int64_t *gl = D.GL + (int64_t)(active ? i : 0) * SD_GAPW * SD_SLOTS;
+    const int64_t *gr = D.GR + (int64_t)(active ? j : 0) * SD_GAPW * SD_SLOTS;
+    GS = GapRows{reinterpret_cast<const int64_t(*)[SD_SLOTS]>(gl),
+                 reinterpret_cast<const int64_t(*)[SD_SLOTS]>(gr)};
+  }
 
   int64_t Bs[SD_SLOTS], PSs[SD_SLOTS];
 #pragma unroll
@@ -1374,8 +1389,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
       Fo.fo_off = Do.fo_off;
       Fo.fi = Do.fi;
       Fo.fi_off = Do.fi_off;
+      const GapStage &og = s_gap[(threadIdx.x >> 5) * NGW + go_k];
       q_slot<G, COUNT>(Fo, Do, P, T, sub, o_a0 + sa, o_b0 + sb, o_i, sa, o_i + g, sb, tm_k, qv,
-                       ops, s_gap[(threadIdx.x >> 5) * NGW + go_k]);
+                       ops, GapRows{og.hl, og.hr});
     }
     const int o_rcell = ((g & (SD_RING - 1)) * (Do.n + 1) + o_i) * SD_SLOTS;
     const int64_t q8[8] = {qv[0], qv[1], qv[2], qv[3], qv[4], qv[5], SD_INF, SD_INF};
