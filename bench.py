@@ -51,8 +51,8 @@ ENERGY_SEED = 1
 # layer pair, from a one-launch ncu capture of a small case of the kernel
 # source with this SHA-256, scaled here to a bench launch by its layer pairs
 # (the procedure is in the design notes).  Any other kernel source: null.
-FILL_DRAM = {"sha256": "f9ccaaba5d17c0d7026083892804f82fdc98d50b7024cfbfa75be884514d09a3",
-             "bytes_per_layer_pair": (144468992 + 12994304) / 14416}
+FILL_DRAM = {"sha256": "0ab2be8e7bd63139a8d6beb7e1c9b308dc6214e8ebd5f40eee573b1e1b715820",
+             "bytes_per_layer_pair": (144442112 + 13218048) / 14416}
 
 
 def parse():
