@@ -51,7 +51,7 @@ ENERGY_SEED = 1
 # layer pair, from a one-launch ncu capture of a small case of the kernel
 # source with this SHA-256, scaled here to a bench launch by its layer pairs
 # (the procedure is in the design notes).  Any other kernel source: null.
-FILL_DRAM = {"sha256": "0ab2be8e7bd63139a8d6beb7e1c9b308dc6214e8ebd5f40eee573b1e1b715820",
+FILL_DRAM = {"sha256": "e720778bea6cbeea918cb701e38f068f547b850a2fae1a0f434ad4217cebedd3",
              "bytes_per_layer_pair": (144442112 + 13218048) / 14416}
 
 

@@ -7,12 +7,16 @@
 // values and exterior values by barriers; here all phases of one layer pair run
 // in the group that owns it, because each only reads smaller spans or the same
 // cell:
+//   stage  gap vectors of both ends (mirrors GL / GR)            spans 0..30 (< g)
 //   H      min path cost a->b (gap cells)                       span g-1
-//   Ihat   inner pair + its loop-side mismatch (two-loop inner)  span g-2
-//   IL     generic internal loops below an outer pair            spans g-2..g-26
+//   Ihat   inner pair + its loop-side mismatch (two-loop inner)  V at span g-2
 //   V_t    typed closed value (Sec. 4.1)                         Q at span g-2
+//   B, WB  Eq. (branch); the bulge term of the cell              V of this cell
+//   X, Y   one-nucleotide-side factors of 1 x n / n x 1 loops    V at span g-1
+//   Af     two-loop factors (1 x n, n x 1, 2x3, 3x2)             X / Y windows, V
+//   IL, K  generic internal loops by loop size                   Ihat spans g..g-26, K at g-2
 //   S2     Eq. (sparse2): edge extension + candidate splits      spans < g
-//   S1,B   Eq. (branch), P_S, S1 = min(B, P_S), strict test B < P_S (Eq. candidates)
+//   S1     P_S, S1 = min(B, P_S), strict test B < P_S (Eq. candidates)
 //   Q_t    hairpin / two-loop / multiloop interior for outer type t (read by V at g+2)
 // The owner of layer pair (i, i+g) is the only writer of C_b for b on layer
 // i+g at span g (Sec. 5 endpoint ownership), and it scans C_b before it
@@ -26,7 +30,7 @@
 // is re-derived afterwards by the traceback from the full tables.
 //
 // The exterior (final-column) values and the traceback run after the fill,
-// one block per design.
+// one 1,024-thread block per design.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
