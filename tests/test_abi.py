@@ -58,3 +58,15 @@ def test_binding_refuses_to_run_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(sd, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         sd.lib()
+
+
+def test_host_only_argument_checks(libsd):
+    """Argument checks that return before any CUDA call: a NULL plan for the
+    scheduling setters, and the message of a bounded-wait timeout."""
+    libsd.sd_plan_set_group.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    libsd.sd_plan_set_streams.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    for group in (0, 8, 16, 32, 7):
+        assert libsd.sd_plan_set_group(None, group) == -1
+    assert libsd.sd_plan_set_streams(None, 2) == -1
+    libsd.sd_strerror.restype = ctypes.c_char_p
+    assert b"wait" in libsd.sd_strerror(-6)
