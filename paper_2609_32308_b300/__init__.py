@@ -396,7 +396,8 @@ class Plan:
             raise SdError(rc, "sd_plan_set_streams")
 
     def autotune(self):
-        """Pick the fastest group size; returns {group: fill ms}."""
+        """Pick the fastest group choice (SD_GROUP_BY_SPAN, 8, 16 or 32 threads
+        per layer pair); returns {group: fill ms}."""
         ms = np.zeros(4, dtype=np.float32)
         rc = lib().sd_plan_autotune(self.handle, _ptr(ms))
         if rc != SD_OK:
