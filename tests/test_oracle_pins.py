@@ -486,3 +486,25 @@ def test_oracle_motifs_empty_inventory_and_infeasible(par1):
                  ("GLSRA", ["GG", "UCU"])):
         assert oracle.run_motifs(par1, p, w, 1.0, m) is None
         assert brute.brute_force(read_params(par1), p, w, 1.0, m) == (None, [])
+
+
+def test_branch_interface_is_the_best_type_plus_ml_intern(par1, P1):
+    """Eq. (branch): B(a, b) = min over pair types t of V_t(a, b) + ML_intern +
+    AU(t), so B - ML_intern is the exterior branch cost min_t V_t + AU(t) (the
+    identity the device exterior pass and traceback read B through), on the
+    oracle's tables of two designs; cells that no type closes stay +inf."""
+    scale = 1 << 32
+    au = np.array([int(x) for x in P1["terminal_au"]], dtype=np.int64)
+    mli = int(P1["ml_intern"])
+    for A, seed, lam in ((14, 41, 4.0), (20, 42, 0.0)):
+        prot = inputs.random_protein(A, seed)
+        w = inputs.random_codon_weights(seed)
+        o = oracle.run(par1, prot, w, lam)
+        fin = o.V < oracle.INF
+        closed = o.B < oracle.INF
+        assert closed.any() and not closed.all()
+        best = np.where(fin, o.V + (mli + au)[None, None, :] * scale, oracle.INF).min(axis=2)
+        assert np.array_equal(np.where(closed, o.B, 0), np.where(closed, best, 0))
+        assert (best[~closed] >= oracle.INF).all()
+        ext = np.where(fin, o.V + au[None, None, :] * scale, oracle.INF).min(axis=2)
+        assert np.array_equal(ext[closed], o.B[closed] - mli * scale)
