@@ -884,70 +884,22 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
     }
     // Two-loop factors Af of this cell (a, b) for the pairs closing one
     // nucleotide outside it (x -> a and b -> y; read by q_slot two spans up).
-    // Everything that does not depend on the outer pair is taken here, once per
+    // Everything that does not depend on the outer pair is taken once per
     // cell: the inner pair, the unpaired nucleotides beyond a or b and their
-    // path costs (from this layer pair's staged gap vectors):
+    // path costs:
     //   [p]    1 x n: l1 = 1 (nucleotide p enters a), the inner pair (a, d) with
     //          d -> u, u on layer lu, l2 = j + 2 - lu >= 3: X(a,u)[p] + H(u -> b)
-    //          + size / asymmetry
+    //          + size / asymmetry (by row, after the slot loop)
     //   [4+r]  n x 1: l2 = 1 (nucleotide r leaves b), the inner pair (c, b) with
     //          w -> c, w on layer lw, l1 = lw - i + 2 >= 3: Y(w,b)[r] + H(a -> w)
-    //          + size / asymmetry
+    //          + size / asymmetry (by column, after the slot loop)
     //   [8]    2 x 3 and 3 x 2: the inner pair's V with its 2x3 mismatch, the
-    //          unpaired edges, size
+    //          unpaired edges, size (here)
     {
       int64_t af[9];
 #pragma unroll
       for (int q = 0; q < 9; q++) af[q] = SD_INF;
       if (ok && g >= 7) {
-        const int im = D.in_mask[a], om = D.out_mask[b];
-        // 1 x n: u on layer lu, l2 = j + 2 - lu in [3, 29], inner span lu - 1 - i >= 5
-        // (narrow layers: by row and column after this loop)
-        const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = SD_W == 2 ? -1 : j - 1;
-        if (ulo <= uhi)
-#pragma unroll 1
-          for (int u = F.ls(ulo) + sub; u < F.ls(uhi + 1); u += G) {
-            const int pu = __ldg(&D.pos[u]);
-            const int lu = pu >> SD_CAND_SHIFT, us = pu & ((1 << SD_CAND_SHIFT) - 1), l2 = j + 2 - lu;
-            const int64_t h = GS.hr[j - lu][us * SD_W + sb];
-            if (!fin(h)) continue;
-            const int64_t base =
-                h + fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1)));
-            const int64_t *xc =
-                D.Xc + ((int64_t)a * 4 * SD_XSPAN + ((lu - i) & (SD_XSPAN - 1))) * SD_W + us;
-#pragma unroll
-            for (int p = 0; p < 4; p++)
-              if ((im >> p) & 1) {
-                const int64_t x = ro(xc + p * SD_XSPAN * SD_W);
-                if (fin(x)) {
-                  upd(af[p], x + base);
-                  TERM(2);
-                }
-              }
-          }
-        // n x 1: w on layer lw, l1 = lw - i + 2 in [3, 29], inner span j - lw - 1 >= 5
-        const int wlo = i + 1, whi = SD_W == 2 ? -1 : min(i + SD_MAXTWO - 3, j - 6);
-        if (wlo <= whi)
-#pragma unroll 1
-          for (int w = F.ls(wlo) + sub; w < F.ls(whi + 1); w += G) {
-            const int pw = __ldg(&D.pos[w]);
-            const int lw = pw >> SD_CAND_SHIFT, ws = pw & ((1 << SD_CAND_SHIFT) - 1), l1 = lw - i + 2;
-            const int64_t h = GS.hl[lw - i][ws * SD_W + sa];
-            if (!fin(h)) continue;
-            const int64_t base =
-                h + fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1)));
-            const int64_t *yr =
-                D.Yr + ((int64_t)b * 4 * SD_XSPAN + ((j - lw) & (SD_XSPAN - 1))) * SD_W + ws;
-#pragma unroll
-            for (int r = 0; r < 4; r++)
-              if ((om >> r) & 1) {
-                const int64_t y = ro(yr + r * SD_XSPAN * SD_W);
-                if (fin(y)) {
-                  upd(af[4 + r], y + base);
-                  TERM(2);
-                }
-              }
-          }
         if (g >= 8) {
           const int64_t e23 = fx(T.interior[5] + T.ninio);
           // 2 x 3: a -> c (p2) on layer i+1; d on layer j-2 -> u (r1) on j-1; H(u -> b)
@@ -992,34 +944,33 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         }
       }
-      const int64_t af8 = SD_W == 2 ? SD_INF : seg_min8<G>(af, sub);
       seg_min<G>(af[8]);
-      if (ok) {
-        int64_t *Afc = D.Af + (int64_t)(rcell + s) * SD_AN;
-        if (SD_W > 2 && sub < 8) Afc[sub] = settle(af8);
-        if (sub == 0) Afc[8] = settle(af[8]);
-      }
+      if (ok && sub == 0) D.Af[(int64_t)(rcell + s) * SD_AN + 8] = settle(af[8]);
     }
   }
-  // Narrow layers: the 1 x n factors Af[p] by row (the state a of slot sa and
-  // both slots of layer j at once: the window of u and the X values are the
-  // same for the row) and the n x 1 factors Af[4 + r] by column (the state b
-  // of slot sb and both slots of layer i: the window of w and the Y values are
-  // the same for the column).  acc[side * 4 + label] holds the two slots of
-  // the other end; the group minimum leaves value (sub & 7) in thread sub.
-  if constexpr (SD_W == 2) {
-    const int kr = (int)__reduce_max_sync(FULL, (unsigned)(active ? max(wa, wb) : 0));
+  // The 1 x n factors Af[p] by row (the state a of slot sa with two slots of
+  // layer j at a time: the window of u and the X values are the same for the
+  // row) and the n x 1 factors Af[4 + r] by column (the state b of slot sb
+  // with two slots of layer i at a time).  Item k of the rows is row k / np of
+  // the slot pair k % np (np pairs of slots at the other end), likewise for
+  // the columns.  acc[side * 4 + label] holds the two slots of the pair; the
+  // group minimum leaves value (sub & 7) in thread sub.
+  {
+    const int npj = SD_W == 2 ? 1 : (wb + 1) / 2, npi = SD_W == 2 ? 1 : (wa + 1) / 2;
+    const int nrow = active ? wa * npj : 0, ncol = active ? wb * npi : 0;
+    const int kr = (int)__reduce_max_sync(FULL, (unsigned)max(nrow, ncol));
 #pragma unroll 1
     for (int k = 0; k < kr; k++) {
-      // row sa = k (1 x n)
+      // row item k: row ra of layer i, slots pb, pb + 1 of layer j (1 x n)
       {
-        const bool ok = active && k < wa;
+        const bool ok = k < nrow;
+        const int ra = ok ? k / npj : 0, pb = ok ? 2 * (k % npj) : 0;
         int64_t acc[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) acc[q] = SD_INF;
         const int ulo = max(i + 6, j - (SD_MAXTWO - 3)), uhi = j - 1;
         if (ok && g >= 7 && ulo <= uhi) {
-          const int a = a0 + k, im = D.in_mask[a];
+          const int a = a0 + ra, im = D.in_mask[a];
           const int uend = F.ls(uhi + 1);
           // 2 states per thread and round, their loads issued together
 #pragma unroll 1
@@ -1031,8 +982,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
               const bool in = uu < uend;
               const int pu = in ? __ldg(&D.pos[uu]) : 0;
               const int lu = pu >> SD_CAND_SHIFT, us = pu & ((1 << SD_CAND_SHIFT) - 1), l2 = j + 2 - lu;
-              h0[v] = in ? GS.hr[j - lu][us * SD_W] : SD_INF;
-              h1[v] = in ? GS.hr[j - lu][us * SD_W + 1] : SD_INF;
+              h0[v] = in ? GS.hr[j - lu][us * SD_W + pb] : SD_INF;
+              h1[v] = in ? GS.hr[j - lu][us * SD_W + pb + 1] : SD_INF;
               e[v] = in ? fx(T.interior[1 + l2] + min(T.maxninio, T.ninio * (l2 - 1))) : 0;
               const bool any = fin(h0[v]) || fin(h1[v]);
               const int64_t *xc =
@@ -1058,19 +1009,20 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         }
         const int64_t v = seg_min8<G>(acc, sub);
-        const int sb = (sub >> 2) & 1;
+        const int sb = pb + ((sub >> 2) & 1);
         if (ok && sub < 8 && sb < wb)
-          D.Af[(int64_t)(rcell + k * SD_W + sb) * SD_AN + (sub & 3)] = settle(v);
+          D.Af[(int64_t)(rcell + ra * SD_W + sb) * SD_AN + (sub & 3)] = settle(v);
       }
-      // column sb = k (n x 1)
+      // column item k: column cb of layer j, slots pb, pb + 1 of layer i (n x 1)
       {
-        const bool ok = active && k < wb;
+        const bool ok = k < ncol;
+        const int cb = ok ? k / npi : 0, pb = ok ? 2 * (k % npi) : 0;
         int64_t acc[8];
 #pragma unroll
         for (int q = 0; q < 8; q++) acc[q] = SD_INF;
         const int wlo = i + 1, whi = min(i + SD_MAXTWO - 3, j - 6);
         if (ok && g >= 7 && wlo <= whi) {
-          const int b = b0 + k, om = D.out_mask[b];
+          const int b = b0 + cb, om = D.out_mask[b];
           const int wend = F.ls(whi + 1);
           // 2 states per thread and round, their loads issued together
 #pragma unroll 1
@@ -1082,8 +1034,8 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
               const bool in = ww < wend;
               const int pw = in ? __ldg(&D.pos[ww]) : 0;
               const int lw = pw >> SD_CAND_SHIFT, ws = pw & ((1 << SD_CAND_SHIFT) - 1), l1 = lw - i + 2;
-              h0[v] = in ? GS.hl[lw - i][ws * SD_W] : SD_INF;
-              h1[v] = in ? GS.hl[lw - i][ws * SD_W + 1] : SD_INF;
+              h0[v] = in ? GS.hl[lw - i][ws * SD_W + pb] : SD_INF;
+              h1[v] = in ? GS.hl[lw - i][ws * SD_W + pb + 1] : SD_INF;
               e[v] = in ? fx(T.interior[l1 + 1] + min(T.maxninio, T.ninio * (l1 - 1))) : 0;
               const bool any = fin(h0[v]) || fin(h1[v]);
               const int64_t *yr =
@@ -1109,9 +1061,9 @@ __global__ void __launch_bounds__(FillShape<G>::threads, G == 32 ? 4 : SD_FILL_M
           }
         }
         const int64_t v = seg_min8<G>(acc, sub);
-        const int sa = (sub >> 2) & 1;
+        const int sa = pb + ((sub >> 2) & 1);
         if (ok && sub < 8 && sa < wa)
-          D.Af[(int64_t)(rcell + sa * SD_W + k) * SD_AN + 4 + (sub & 3)] = settle(v);
+          D.Af[(int64_t)(rcell + sa * SD_W + cb) * SD_AN + 4 + (sub & 3)] = settle(v);
       }
     }
   }
