@@ -51,8 +51,8 @@ ENERGY_SEED = 1
 # layer pair, from a one-launch ncu capture of a small case of the kernel
 # source with this SHA-256, scaled here to a bench launch by its layer pairs
 # (the procedure is in the design notes).  Any other kernel source: null.
-FILL_DRAM = {"sha256": "e720778bea6cbeea918cb701e38f068f547b850a2fae1a0f434ad4217cebedd3",
-             "bytes_per_layer_pair": (144442112 + 13218048) / 14416}
+FILL_DRAM = {"sha256": "56f3c447d859fa547ef0810866e1b50218b8fd478e7a34b017604cc7e551903f",
+             "bytes_per_layer_pair": (144475136 + 13080576) / 14416}
 
 
 def parse():
