@@ -247,3 +247,37 @@ def test_presized_plan_same_speed(sd, E1):
     assert keys["pred"] == keys["plain"]
     assert room["pred"] < room["plain"] and nbytes["pred"] < nbytes["plain"]
     assert fill["pred"] <= 1.05 * fill["plain"] + 1.0, fill
+
+
+def test_predicted_schedule_no_slower_on_a_mixed_batch(sd, E1):
+    """The predicted schedule (designs over two streams, longest predicted work
+    first) on a mixed-length batch: its replayed run takes no longer than the
+    one-stream run of the same presized plan (5% slack for timing noise), and
+    every design is identical."""
+    import torch
+    from paper_2609_32308_b300 import retention
+    lengths = inputs.lengths_log_uniform(24, 50, 600, seed=21)
+    batch = inputs.protein_batch(lengths, seed=21)
+    p = sd.Plan(E1, [b[0] for b in batch], np.stack([b[1] for b in batch]),
+                [b[2] for b in batch], predictor=retention.load(), margin=2.0)
+    try:
+        stream = torch.cuda.current_stream()
+        ms, keys = {}, {}
+        for k in (1, 2):
+            p.streams = k
+            p.set_graph(True)
+            p.run(stream)
+            keys[k] = [_design_keys(r) for r in p.results()]
+            ts = []
+            for _ in range(3):
+                t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                t0.record(stream)
+                p.run(stream)
+                t1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(t0.elapsed_time(t1))
+            ms[k] = min(ts)
+        assert keys[2] == keys[1]
+        assert ms[2] <= 1.05 * ms[1] + 1.0, ms
+    finally:
+        p.free()
